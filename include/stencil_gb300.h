@@ -1,0 +1,156 @@
+/*
+ * stencil_gb300.h -- C ABI of the GB300 (sm_103a) stencil sweep library.
+ *
+ * The operations are those of Malas, Ltaief, Hager, Keyes, "Towards energy
+ * efficiency and maximum computational intensity for stencil algorithms using
+ * wavefront diamond temporal blocking" (arXiv:1410.5561):
+ *   - Section I (problem statement): a sweep updates every interior point of a
+ *     3D grid from its neighbours' previous values; sweeps repeat over many
+ *     time steps, Jacobi-style, with two domain-sized arrays (Section I-A).
+ *   - Listing 1: 7-point constant-coefficient stencil (scalars c0, c1).
+ *   - Listing 2: 7-point variable-coefficient stencil (7 arrays C0..C6;
+ *     C1 +x, C2 -x, C3 +y, C4 -y, C5 +z, C6 -z).
+ *   - Listing 3: 25-point (radius 4) axis-symmetric variable-coefficient
+ *     stencil (13 arrays; C00 centre, C(3(d-1)+a+1) weighs the pair at
+ *     distance d on axis a = x, y, z).
+ *   - Section II-A / III: the temporally blocked (wavefront diamond) schedule,
+ *     selected with stencil_set_tuning(STENCIL_BLOCKED, ...).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: STENCIL_OK (0) or a negative stencil_status. Nothing
+ *     throws across the ABI. stencil_strerror() names a status.
+ *   - Streams: every device operation is enqueued on the cudaStream_t given
+ *     to stencil_create (0 = legacy default stream) and is asynchronous with
+ *     respect to the host unless stated otherwise.
+ *   - Memory: the library never allocates device memory. The caller allocates
+ *     the two field arrays, the coefficient arrays and the workspace (sizes
+ *     from stencil_layout_of / stencil_workspace_bytes) and keeps them alive
+ *     until the work enqueued on them has finished. Device pointers must be
+ *     16-byte aligned.
+ *   - Grid layout (element index, shared by the field and coefficient arrays
+ *     of one grid; R = halo width = stencil radius):
+ *       interior point (i, j, k), 0 <= i < nx, 0 <= j < ny, 0 <= k < nz, is at
+ *       ((k + R) * pitch_y + (j + R)) * pitch_x + x_offset + i
+ *     with pitch_y = ny + 2R and planes = nz + 2R. Cells that are not interior
+ *     form the Dirichlet halo (plus row padding); stencil_set_field fills them.
+ *   - Dense arrays passed to set_field / set_coeffs / get_field hold the
+ *     interior only, shaped (nz, ny, nx), x fastest, in the array's dtype.
+ */
+#ifndef STENCIL_GB300_H
+#define STENCIL_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct stencil_grid* stencil_t; /* opaque, owned by the library */
+
+enum stencil_kind { STENCIL_7PT_CONST = 0, STENCIL_7PT_VAR = 1, STENCIL_25PT_VAR = 2 };
+enum stencil_dtype { STENCIL_F32 = 0, STENCIL_F64 = 1, STENCIL_BF16 = 2 };
+enum stencil_scheme { STENCIL_PLAIN = 0, STENCIL_BLOCKED = 1, STENCIL_AUTO = 2 };
+enum stencil_where { STENCIL_HOST = 0, STENCIL_DEVICE = 1 };
+enum stencil_array { STENCIL_FIELD_ARRAY = 0, STENCIL_COEF_ARRAY = 1 };
+
+enum stencil_status {
+    STENCIL_OK = 0,
+    STENCIL_EINVAL = -1,   /* bad argument: shape, dtype, pointer alignment, tuning */
+    STENCIL_ENOSMEM = -2,  /* blocked tuning needs more shared memory than one CTA may have */
+    STENCIL_ETIMEOUT = -3, /* a bounded device-side wait gave up (see stencil_status) */
+    STENCIL_ECUDA = -4,    /* a CUDA runtime call failed */
+    STENCIL_EUNBOUND = -5, /* arrays not bound yet */
+    STENCIL_ENOTSUP = -6   /* combination not implemented */
+};
+
+/* Blocked-schedule tunables (Section II-A, III-A): dw = diamond width D_w
+ * along y (a multiple of 2R), nf = frontlines N_F (z planes per time level per
+ * wavefront step), warps = warps per CTA, xsplit = CTAs per thread-block
+ * cluster; the cluster is the thread group that shares one extruded diamond,
+ * its CTAs splitting x (1..16). */
+typedef struct {
+    int dw;
+    int nf;
+    int warps;
+    int xsplit;
+} stencil_tuning;
+
+typedef struct {
+    int radius;        /* R */
+    int elem_bytes;    /* bytes per element of this array */
+    int x_offset;      /* elements before interior x = 0 in each row */
+    int pitch_x;       /* elements per row */
+    int pitch_y;       /* rows per plane (ny + 2R) */
+    int planes;        /* nz + 2R */
+    size_t bytes;      /* pitch_x * pitch_y * planes * elem_bytes */
+} stencil_layout;
+
+/* Create a grid handle. kind: stencil_kind. nx, ny, nz >= 1 interior sizes.
+ * field_dtype: STENCIL_F32 or STENCIL_F64. coef_dtype: equal to field_dtype,
+ * or STENCIL_BF16 with an FP32 field (coefficients stored in BF16, widened
+ * exactly to FP32 in registers); ignored for STENCIL_7PT_CONST. cuda_stream:
+ * a cudaStream_t (may be NULL). *out receives the handle. */
+int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_dtype, int coef_dtype,
+                   void* cuda_stream);
+
+/* Layout of the field (which = STENCIL_FIELD_ARRAY) or of one coefficient
+ * array (STENCIL_COEF_ARRAY) of this grid. */
+int stencil_layout_of(stencil_t h, int which, stencil_layout* out);
+
+/* Bytes of device workspace run() needs (caller-allocated, passed to bind;
+ * may be 0). */
+size_t stencil_workspace_bytes(stencil_t h);
+
+/* Bind caller-owned device arrays: field_a, field_b (field layout; ping-pong
+ * pair), coef[0..n_c-1] (coefficient layout; NULL for 7PT_CONST), workspace
+ * (stencil_workspace_bytes, may be NULL when that is 0). Borrowed, not owned. */
+int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, void* workspace);
+
+/* Coefficients. 7PT_CONST: scalars = {c0, c1} (host), arrays ignored.
+ * Variable kinds: arrays[m] = dense interior array m (coef dtype), on the host
+ * (where = STENCIL_HOST) or device (STENCIL_DEVICE); copied into the bound
+ * coefficient arrays, whose halo is set to 0. */
+int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* arrays, int where);
+
+/* Initial field u_0: dense interior src (field dtype, host or device). Both
+ * field arrays get every non-interior cell set to halo_value (the Dirichlet
+ * value, never written again by a sweep); src goes to the interior of field_a,
+ * which becomes the current array (time 0). */
+int stencil_set_field(stencil_t h, const void* src, double halo_value, int where);
+
+/* Select the schedule used by run(): STENCIL_PLAIN (one launch per step),
+ * STENCIL_BLOCKED with *tuning (NULL: library default), or STENCIL_AUTO (the
+ * library default blocked tuning when it fits, else plain). Returns
+ * STENCIL_ENOSMEM / STENCIL_EINVAL for an infeasible blocked tuning. */
+int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning);
+
+/* Advance the current field by T >= 0 Jacobi steps (Listings 1-3 applied T
+ * times). Asynchronous on the handle's stream. Afterwards field_a holds u_T if
+ * (initial parity + T) is even, field_b otherwise (see stencil_parity). */
+int stencil_run(stencil_t h, int T);
+
+/* 0 if field_a holds the current time level, 1 if field_b does. */
+int stencil_parity(stencil_t h);
+
+/* Copy the current field's interior to dense dst (host or device). With
+ * where = STENCIL_HOST the call waits for the stream. */
+int stencil_get_field(stencil_t h, void* dst, int where);
+
+/* Shared-memory bytes per CTA the blocked kernel needs for a tuning (0 if the
+ * tuning is malformed); the device limit is cudaDevAttrMaxSharedMemoryPerBlockOptin. */
+size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning);
+
+/* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error. */
+int stencil_sync(stencil_t h);
+
+/* Static description of a status code. */
+const char* stencil_strerror(int status);
+
+/* Release the handle (not the caller's arrays). */
+int stencil_destroy(stencil_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_GB300_H */

@@ -1,0 +1,307 @@
+// C-ABI layer: argument checks, layout, host<->device copies and dispatch to
+// the sweep kernels. Declarations and contracts are in include/stencil_gb300.h.
+#include <stdint.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/stencil_gb300.h"
+#include "internal.h"
+
+using namespace stg;
+
+struct stencil_grid {
+    int kind, fdt, cdt;
+    Layout L;
+    cudaStream_t stream;
+    void* field[2];
+    void* coef[13];
+    void* ws;
+    bool bound;
+    double c0, c1, halo;
+    int parity;
+    int scheme;
+    BlockedTune tune;
+    bool tune_set;
+};
+
+static int from_cuda(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static SweepArgs args_of(const stencil_grid* h) {
+    SweepArgs a{};
+    a.kind = h->kind;
+    a.fdt = h->fdt;
+    a.cdt = h->cdt;
+    a.L = h->L;
+    for (int m = 0; m < 13; ++m) a.coef[m] = h->coef[m];
+    a.c0 = h->c0;
+    a.c1 = h->c1;
+    a.halo = h->halo;
+    return a;
+}
+
+// Default blocked tuning: D_w = 8 (R = 1) or 16 (R = 4), one frontline, 8 warps,
+// x split so that each CTA holds at most 128 FP32 (64 FP64) columns; D_w is
+// halved until the rings fit the shared-memory opt-in limit.
+static BlockedTune default_tune(const stencil_grid* h) {
+    BlockedTune t{};
+    int R = kind_radius(h->kind);
+    int eb = dtype_bytes(h->fdt);
+    int maxcols = 512 / eb;
+    t.dw = R == 1 ? 8 : 16;
+    t.nf = 1;
+    t.warps = 8;
+    t.cx = (h->L.nx + maxcols - 1) / maxcols;
+    if (t.cx < 1) t.cx = 1;
+    if (t.cx > 16) t.cx = 16;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 0;
+    SweepArgs a = args_of(h);
+    while (t.dw > 2 * R && (blocked_smem_bytes(a, t) == 0 || blocked_smem_bytes(a, t) > (size_t)optin)) t.dw /= 2;
+    return t;
+}
+
+static int check_tune(const stencil_grid* h, const BlockedTune& t) {
+    SweepArgs a = args_of(h);
+    size_t need = blocked_smem_bytes(a, t);
+    if (need == 0) return STENCIL_EINVAL;
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return STENCIL_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return STENCIL_ECUDA;
+    if (need > (size_t)optin) return STENCIL_ENOSMEM;
+    return STENCIL_OK;
+}
+
+extern "C" {
+
+int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_dtype, int coef_dtype,
+                   void* cuda_stream) {
+    if (!out) return STENCIL_EINVAL;
+    *out = nullptr;
+    if (kind < STENCIL_7PT_CONST || kind > STENCIL_25PT_VAR) return STENCIL_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1) return STENCIL_EINVAL;
+    if (field_dtype != STENCIL_F32 && field_dtype != STENCIL_F64) return STENCIL_EINVAL;
+    if (kind == STENCIL_7PT_CONST) coef_dtype = field_dtype;
+    if (coef_dtype != field_dtype && !(field_dtype == STENCIL_F32 && coef_dtype == STENCIL_BF16))
+        return STENCIL_EINVAL;
+    const int R = kind_radius(kind);
+    const int eb = dtype_bytes(field_dtype);
+    const int V = 16 / eb;
+    const int J = (R + V - 1) / V;
+    const long long rowal = 128 / eb;  // 128-byte rows for the field
+    long long xo = (long long)J * V;
+    long long px = xo + ((nx + V - 1) / V) * (long long)V + xo;
+    px = ((px + rowal - 1) / rowal) * rowal;
+    long long py = (long long)ny + 2 * R, pz = (long long)nz + 2 * R;
+    if (px > (1LL << 30) || py > (1LL << 30) || pz > (1LL << 30)) return STENCIL_EINVAL;
+    stencil_grid* h = new (std::nothrow) stencil_grid();
+    if (!h) return STENCIL_EINVAL;
+    h->kind = kind;
+    h->fdt = field_dtype;
+    h->cdt = coef_dtype;
+    h->L.nx = nx;
+    h->L.ny = ny;
+    h->L.nz = nz;
+    h->L.R = R;
+    h->L.xo = (int)xo;
+    h->L.px = (int)px;
+    h->L.py = (int)py;
+    h->L.pz = (int)pz;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->c0 = 0.4;
+    h->c1 = 0.1;
+    h->halo = 0.0;
+    h->parity = 0;
+    h->scheme = STENCIL_PLAIN;
+    h->tune_set = false;
+    *out = h;
+    return STENCIL_OK;
+}
+
+int stencil_layout_of(stencil_t h, int which, stencil_layout* out) {
+    if (!h || !out) return STENCIL_EINVAL;
+    if (which != STENCIL_FIELD_ARRAY && which != STENCIL_COEF_ARRAY) return STENCIL_EINVAL;
+    if (which == STENCIL_COEF_ARRAY && h->kind == STENCIL_7PT_CONST) return STENCIL_EINVAL;
+    int eb = dtype_bytes(which == STENCIL_FIELD_ARRAY ? h->fdt : h->cdt);
+    out->radius = h->L.R;
+    out->elem_bytes = eb;
+    out->x_offset = h->L.xo;
+    out->pitch_x = h->L.px;
+    out->pitch_y = h->L.py;
+    out->planes = h->L.pz;
+    out->bytes = h->L.count() * (size_t)eb;
+    return STENCIL_OK;
+}
+
+size_t stencil_workspace_bytes(stencil_t h) {
+    (void)h;
+    return 0;
+}
+
+int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, void* workspace) {
+    if (!h || !field_a || !field_b || field_a == field_b) return STENCIL_EINVAL;
+    if (!aligned16(field_a) || !aligned16(field_b)) return STENCIL_EINVAL;
+    int nc = kind_ncoef(h->kind);
+    if (nc > 0 && !coef) return STENCIL_EINVAL;
+    for (int m = 0; m < nc; ++m)
+        if (!coef[m] || !aligned16(coef[m])) return STENCIL_EINVAL;
+    h->field[0] = field_a;
+    h->field[1] = field_b;
+    for (int m = 0; m < 13; ++m) h->coef[m] = m < nc ? coef[m] : nullptr;
+    h->ws = workspace;
+    h->bound = true;
+    return STENCIL_OK;
+}
+
+static cudaError_t copy_interior(const stencil_grid* h, int eb, const void* dense, void* padded, bool to_padded) {
+    const Layout& L = h->L;
+    cudaMemcpy3DParms p{};
+    cudaPitchedPtr dn = make_cudaPitchedPtr(const_cast<void*>(dense), (size_t)L.nx * eb, (size_t)L.nx, (size_t)L.ny);
+    cudaPitchedPtr pd = make_cudaPitchedPtr(padded, (size_t)L.px * eb, (size_t)L.px, (size_t)L.py);
+    if (to_padded) {
+        p.srcPtr = dn;
+        p.dstPtr = pd;
+        p.dstPos = make_cudaPos((size_t)L.xo * eb, (size_t)L.R, (size_t)L.R);
+    } else {
+        p.srcPtr = pd;
+        p.srcPos = make_cudaPos((size_t)L.xo * eb, (size_t)L.R, (size_t)L.R);
+        p.dstPtr = dn;
+    }
+    p.extent = make_cudaExtent((size_t)L.nx * eb, (size_t)L.ny, (size_t)L.nz);
+    p.kind = cudaMemcpyDefault;
+    return cudaMemcpy3DAsync(&p, h->stream);
+}
+
+int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* arrays, int where) {
+    if (!h) return STENCIL_EINVAL;
+    if (where != STENCIL_HOST && where != STENCIL_DEVICE) return STENCIL_EINVAL;
+    if (h->kind == STENCIL_7PT_CONST) {
+        if (!scalars) return STENCIL_EINVAL;
+        h->c0 = scalars[0];
+        h->c1 = scalars[1];
+        return STENCIL_OK;
+    }
+    if (!h->bound) return STENCIL_EUNBOUND;
+    if (!arrays) return STENCIL_EINVAL;
+    int nc = kind_ncoef(h->kind);
+    int eb = dtype_bytes(h->cdt);
+    for (int m = 0; m < nc; ++m) {
+        if (!arrays[m]) return STENCIL_EINVAL;
+        cudaError_t e = fill_value(h->coef[m], h->L.count(), h->cdt, 0.0, h->stream);
+        if (e != cudaSuccess) return STENCIL_ECUDA;
+        e = copy_interior(h, eb, arrays[m], h->coef[m], true);
+        if (e != cudaSuccess) return STENCIL_ECUDA;
+    }
+    return STENCIL_OK;
+}
+
+int stencil_set_field(stencil_t h, const void* src, double halo_value, int where) {
+    if (!h || !src) return STENCIL_EINVAL;
+    if (where != STENCIL_HOST && where != STENCIL_DEVICE) return STENCIL_EINVAL;
+    if (!h->bound) return STENCIL_EUNBOUND;
+    for (int i = 0; i < 2; ++i) {
+        cudaError_t e = fill_value(h->field[i], h->L.count(), h->fdt, halo_value, h->stream);
+        if (e != cudaSuccess) return STENCIL_ECUDA;
+    }
+    cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), src, h->field[0], true);
+    if (e != cudaSuccess) return STENCIL_ECUDA;
+    h->halo = halo_value;
+    h->parity = 0;
+    return STENCIL_OK;
+}
+
+int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning) {
+    if (!h) return STENCIL_EINVAL;
+    if (scheme == STENCIL_PLAIN) {
+        h->scheme = STENCIL_PLAIN;
+        return STENCIL_OK;
+    }
+    if (scheme != STENCIL_BLOCKED && scheme != STENCIL_AUTO) return STENCIL_EINVAL;
+    BlockedTune t = default_tune(h);
+    if (tuning && scheme == STENCIL_BLOCKED) {
+        t.dw = tuning->dw;
+        t.nf = tuning->nf;
+        t.warps = tuning->warps;
+        t.cx = tuning->xsplit;
+    }
+    int rc = check_tune(h, t);
+    if (rc != STENCIL_OK) {
+        if (scheme == STENCIL_AUTO) {
+            h->scheme = STENCIL_PLAIN;
+            return STENCIL_OK;
+        }
+        return rc;
+    }
+    h->scheme = STENCIL_BLOCKED;
+    h->tune = t;
+    h->tune_set = true;
+    return STENCIL_OK;
+}
+
+int stencil_run(stencil_t h, int T) {
+    if (!h || T < 0) return STENCIL_EINVAL;
+    if (!h->bound) return STENCIL_EUNBOUND;
+    if (T == 0) return STENCIL_OK;
+    SweepArgs a = args_of(h);
+    if (h->scheme == STENCIL_BLOCKED) {
+        cudaError_t e = blocked_run(a, h->field, h->parity, T, h->tune, h->stream);
+        if (e == cudaErrorInvalidValue) return STENCIL_EINVAL;
+        if (e != cudaSuccess) return STENCIL_ECUDA;
+    } else {
+        for (int t = 0; t < T; ++t) {
+            int p = (h->parity + t) & 1;
+            cudaError_t e = plain_step(a, h->field[p], h->field[p ^ 1], h->stream);
+            if (e != cudaSuccess) return STENCIL_ECUDA;
+        }
+    }
+    h->parity = (h->parity + T) & 1;
+    return STENCIL_OK;
+}
+
+int stencil_parity(stencil_t h) { return h ? h->parity : STENCIL_EINVAL; }
+
+int stencil_get_field(stencil_t h, void* dst, int where) {
+    if (!h || !dst) return STENCIL_EINVAL;
+    if (where != STENCIL_HOST && where != STENCIL_DEVICE) return STENCIL_EINVAL;
+    if (!h->bound) return STENCIL_EUNBOUND;
+    cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), dst, h->field[h->parity], false);
+    if (e != cudaSuccess) return STENCIL_ECUDA;
+    if (where == STENCIL_HOST) return from_cuda(cudaStreamSynchronize(h->stream));
+    return STENCIL_OK;
+}
+
+size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning) {
+    if (!h || !tuning) return 0;
+    BlockedTune t{tuning->dw, tuning->nf, tuning->warps, tuning->xsplit};
+    return blocked_smem_bytes(args_of(h), t);
+}
+
+int stencil_sync(stencil_t h) {
+    if (!h) return STENCIL_EINVAL;
+    return from_cuda(cudaStreamSynchronize(h->stream));
+}
+
+const char* stencil_strerror(int status) {
+    switch (status) {
+        case STENCIL_OK: return "ok";
+        case STENCIL_EINVAL: return "invalid argument";
+        case STENCIL_ENOSMEM: return "blocked tuning exceeds the shared-memory limit";
+        case STENCIL_ETIMEOUT: return "device-side wait timed out";
+        case STENCIL_ECUDA: return "CUDA runtime error";
+        case STENCIL_EUNBOUND: return "arrays not bound";
+        case STENCIL_ENOTSUP: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+int stencil_destroy(stencil_t h) {
+    if (!h) return STENCIL_EINVAL;
+    delete h;
+    return STENCIL_OK;
+}
+
+}  // extern "C"

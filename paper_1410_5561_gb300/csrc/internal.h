@@ -1,0 +1,49 @@
+// Internal interface between the C-ABI layer (api.cu) and the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace stg {
+
+enum DType { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
+
+inline int dtype_bytes(int dt) { return dt == DT_F64 ? 8 : (dt == DT_F32 ? 4 : 2); }
+inline int kind_radius(int kind) { return kind == K25V ? 4 : 1; }
+inline int kind_ncoef(int kind) { return kind == K7C ? 0 : (kind == K7V ? 7 : 13); }
+
+// Everything a sweep kernel needs to know about one grid.
+struct SweepArgs {
+    int kind;              // K7C / K7V / K25V
+    int fdt;               // field dtype: DT_F32 or DT_F64
+    int cdt;               // coefficient dtype: DT_F32, DT_F64 or DT_BF16
+    Layout L;
+    const void* coef[13];  // padded coefficient arrays (device)
+    double c0, c1;         // Listing 1 scalars (7-point constant)
+    double halo;           // Dirichlet value of every halo cell
+};
+
+// Blocked-sweep tunables (D_w, N_F, warps per CTA, CTAs per cluster along x).
+struct BlockedTune {
+    int dw;       // diamond width in y (multiple of 2R)
+    int nf;       // frontlines: z-planes per level per wavefront step
+    int warps;    // warps per CTA
+    int cx;       // CTAs per cluster, splitting x
+};
+
+// One plain step: dst(interior) = A src.
+cudaError_t plain_step(const SweepArgs& a, const void* src, void* dst, cudaStream_t s);
+
+// Fill n elements of dtype dt at p with value v.
+cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s);
+
+// Temporally blocked run of T steps from parity p0 (array (p0 + t) & 1 holds u_t).
+// Returns cudaErrorInvalidValue for an infeasible tuning, after checking it on the host.
+cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T,
+                        const BlockedTune& tune, cudaStream_t s);
+
+// Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
+size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);
+
+}  // namespace stg

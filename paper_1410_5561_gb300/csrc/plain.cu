@@ -1,0 +1,168 @@
+// Plain one-step-per-pass streaming sweep (the analog of the paper's spatially
+// blocked baseline, Section IV, "Spt. Blk."): every launch reads u_t once and
+// writes u_{t+1} once, so it moves 2*s_f + n_c*s_c bytes per LUP at best.
+//
+// Thread mapping: a warp covers 32 vectors of V = 16/sizeof(field) consecutive
+// x values (128-bit accesses); a CTA stacks BY warps along y; each thread walks
+// a chunk of z planes and keeps the 2R+1 planes of its own column in a
+// register ring, so each z-neighbour is loaded once. x- and y-neighbours are
+// plain aligned vector loads that hit L1/L2 (they are re-read by the
+// neighbouring threads); coefficients stream through with evict-first loads.
+#include "internal.h"
+
+namespace stg {
+
+template <typename TC>
+struct CoefPtrs {
+    const TC* c[13];
+};
+
+template <int KIND, typename TF, typename TC, int BY>
+__global__ void __launch_bounds__(32 * BY)
+plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, CoefPtrs<TC> C,
+                   TF c0, TF c1, int zchunk) {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr int NC = KindTraits<KIND>::NC;
+    constexpr int V = 16 / sizeof(TF);
+    constexpr int J = (R + V - 1) / V;  // neighbour vectors needed on each side along x
+    const int i0 = (blockIdx.x * 32 + threadIdx.x) * V;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i0 >= L.nx || j >= L.ny) return;
+    const int k0 = blockIdx.z * zchunk;
+    const int k1 = min(L.nz, k0 + zchunk);
+    if (k0 >= k1) return;
+    const size_t sy = (size_t)L.px;
+    const size_t sz = L.plane();
+    size_t base = L.at(i0, j, k0);
+
+    Vec<TF, V> ring[2 * R + 1];  // planes k-R .. k+R of this thread's column
+#pragma unroll
+    for (int r = 0; r < 2 * R; ++r) ring[r] = ldv<TF, V>(src + base + (ptrdiff_t)(r - R) * (ptrdiff_t)sz);
+
+    for (int k = k0; k < k1; ++k, base += sz) {
+        ring[2 * R] = ldv<TF, V>(src + base + (size_t)R * sz);
+        // x line around the vector: [i0 - J*V, i0 + (J+1)*V)
+        TF xl[(2 * J + 1) * V];
+#pragma unroll
+        for (int q = -J; q <= J; ++q) {
+            Vec<TF, V> w = (q == 0) ? ring[R] : ldv<TF, V>(src + base + (ptrdiff_t)q * V);
+#pragma unroll
+            for (int e = 0; e < V; ++e) xl[(q + J) * V + e] = w.v[e];
+        }
+        Vec<TF, V> yp[R], ym[R];
+#pragma unroll
+        for (int r = 1; r <= R; ++r) {
+            yp[r - 1] = ldv<TF, V>(src + base + (size_t)r * sy);
+            ym[r - 1] = ldv<TF, V>(src + base - (size_t)r * sy);
+        }
+        Vec<TC, V> cv[NC > 0 ? NC : 1];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) cv[m] = ldv_stream<TC, V>(C.c[m] + base);
+
+        Vec<TF, V> out;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int xc = J * V + e;
+            if constexpr (KIND == K7C) {
+                out.v[e] = upd7c<TF>(c0, c1, ring[R].v[e], xl[xc + 1], xl[xc - 1], yp[0].v[e],
+                                     ym[0].v[e], ring[R + 1].v[e], ring[R - 1].v[e]);
+            } else if constexpr (KIND == K7V) {
+                TF c[7];
+#pragma unroll
+                for (int m = 0; m < 7; ++m) c[m] = Cvt<TF, TC>::f(cv[m].v[e]);
+                out.v[e] = upd7v<TF>(c, ring[R].v[e], xl[xc + 1], xl[xc - 1], yp[0].v[e], ym[0].v[e],
+                                     ring[R + 1].v[e], ring[R - 1].v[e]);
+            } else {
+                TF c[13], xp[4], xm[4], ypp[4], ymm[4], zp[4], zm[4];
+#pragma unroll
+                for (int m = 0; m < 13; ++m) c[m] = Cvt<TF, TC>::f(cv[m].v[e]);
+#pragma unroll
+                for (int d = 0; d < 4; ++d) {
+                    xp[d] = xl[xc + d + 1];
+                    xm[d] = xl[xc - d - 1];
+                    ypp[d] = yp[d].v[e];
+                    ymm[d] = ym[d].v[e];
+                    zp[d] = ring[R + d + 1].v[e];
+                    zm[d] = ring[R - d - 1].v[e];
+                }
+                out.v[e] = upd25v<TF>(c, ring[R].v[e], xp, xm, ypp, ymm, zp, zm);
+            }
+        }
+        if (i0 + V <= L.nx) {
+            stv<TF, V>(dst + base, out);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (i0 + e < L.nx) dst[base + e] = out.v[e];
+        }
+#pragma unroll
+        for (int r = 0; r < 2 * R; ++r) ring[r] = ring[r + 1];
+    }
+}
+
+template <int KIND, typename TF, typename TC>
+static cudaError_t launch_plain(const SweepArgs& a, const void* src, void* dst, cudaStream_t s) {
+    constexpr int BY = 8;
+    constexpr int V = 16 / sizeof(TF);
+    const Layout& L = a.L;
+    if (L.nx == 0 || L.ny == 0 || L.nz == 0) return cudaSuccess;
+    CoefPtrs<TC> C{};
+    for (int m = 0; m < KindTraits<KIND>::NC; ++m) C.c[m] = static_cast<const TC*>(a.coef[m]);
+    dim3 block(32, BY);
+    unsigned gx = (unsigned)((L.nx + 32 * V - 1) / (32 * V));
+    unsigned gy = (unsigned)((L.ny + BY - 1) / BY);
+    // Enough z chunks for about 8 CTAs of 256 threads per SM over 152 SMs,
+    // without making chunks shorter than 16 planes (ring warm-up re-reads 2R planes).
+    long long xy = (long long)gx * gy;
+    int want = (int)((8LL * 152 + xy - 1) / xy);
+    int maxchunks = (L.nz + 15) / 16;
+    int nchunks = want < 1 ? 1 : (want > maxchunks ? maxchunks : want);
+    if (nchunks < 1) nchunks = 1;
+    int zchunk = (L.nz + nchunks - 1) / nchunks;
+    nchunks = (L.nz + zchunk - 1) / zchunk;
+    dim3 grid(gx, gy, (unsigned)nchunks);
+    plain_sweep_kernel<KIND, TF, TC, BY><<<grid, block, 0, s>>>(
+        L, static_cast<const TF*>(src), static_cast<TF*>(dst), C, (TF)a.c0, (TF)a.c1, zchunk);
+    return cudaGetLastError();
+}
+
+cudaError_t plain_step(const SweepArgs& a, const void* src, void* dst, cudaStream_t s) {
+    switch (a.kind) {
+        case K7C:
+            if (a.fdt == DT_F32) return launch_plain<K7C, float, float>(a, src, dst, s);
+            if (a.fdt == DT_F64) return launch_plain<K7C, double, double>(a, src, dst, s);
+            break;
+        case K7V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) return launch_plain<K7V, float, float>(a, src, dst, s);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
+                return launch_plain<K7V, float, __nv_bfloat16>(a, src, dst, s);
+            if (a.fdt == DT_F64 && a.cdt == DT_F64) return launch_plain<K7V, double, double>(a, src, dst, s);
+            break;
+        case K25V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) return launch_plain<K25V, float, float>(a, src, dst, s);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
+                return launch_plain<K25V, float, __nv_bfloat16>(a, src, dst, s);
+            if (a.fdt == DT_F64 && a.cdt == DT_F64) return launch_plain<K25V, double, double>(a, src, dst, s);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ fill
+template <typename T>
+__global__ void fill_kernel(T* __restrict__ p, size_t n, T v) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    unsigned blocks = (unsigned)((n + 255) / 256);
+    if (blocks > 152u * 16u) blocks = 152u * 16u;
+    if (dt == DT_F32) fill_kernel<float><<<blocks, 256, 0, s>>>((float*)p, n, (float)v);
+    else if (dt == DT_F64) fill_kernel<double><<<blocks, 256, 0, s>>>((double*)p, n, v);
+    else fill_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((__nv_bfloat16*)p, n, __double2bfloat16(v));
+    return cudaGetLastError();
+}
+
+}  // namespace stg

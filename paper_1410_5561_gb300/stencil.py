@@ -1,0 +1,160 @@
+"""Python face of the C ABI: one :class:`Stencil` per grid, torch tensors as device memory.
+
+Every compute step runs in the CUDA library; this module only allocates the
+arrays the library asks for (through torch), passes pointers and sizes, and
+builds strided views of the padded layout.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib as C
+
+KINDS = {"7pt_const": C.STENCIL_7PT_CONST, "7pt_var": C.STENCIL_7PT_VAR,
+         "25pt_var": C.STENCIL_25PT_VAR}
+RADIUS = {C.STENCIL_7PT_CONST: 1, C.STENCIL_7PT_VAR: 1, C.STENCIL_25PT_VAR: 4}
+NCOEF = {C.STENCIL_7PT_CONST: 0, C.STENCIL_7PT_VAR: 7, C.STENCIL_25PT_VAR: 13}
+DTYPES = {torch.float32: C.STENCIL_F32, torch.float64: C.STENCIL_F64, torch.bfloat16: C.STENCIL_BF16}
+SCHEMES = {"plain": C.STENCIL_PLAIN, "blocked": C.STENCIL_BLOCKED, "auto": C.STENCIL_AUTO}
+
+
+def kind_id(kind) -> int:
+    return KINDS[kind] if isinstance(kind, str) else int(kind)
+
+
+@dataclass
+class Tuning:
+    """Blocked-schedule tunables: diamond width D_w, frontlines N_F, warps per CTA,
+    CTAs per cluster along x (Section II-A's thread group)."""
+    dw: int
+    nf: int = 1
+    warps: int = 8
+    xsplit: int = 1
+
+    def c(self) -> C.stencil_tuning:
+        return C.stencil_tuning(self.dw, self.nf, self.warps, self.xsplit)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Stencil:
+    """One grid: two field arrays (ping-pong), coefficient arrays, workspace."""
+
+    def __init__(self, kind, nx: int, ny: int, nz: int, dtype=torch.float32, coef_dtype=None,
+                 device=None, stream: torch.cuda.Stream | None = None):
+        self.kind = kind_id(kind)
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.dtype = dtype
+        self.coef_dtype = coef_dtype if coef_dtype is not None else dtype
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        C.call("stencil_create", ctypes.byref(h), self.kind, self.nx, self.ny, self.nz,
+               DTYPES[dtype], DTYPES[self.coef_dtype], ctypes.c_void_p(self.stream.cuda_stream))
+        self._h = h
+        self.layout = self._layout(C.STENCIL_FIELD_ARRAY)
+        lay = self.layout
+        n = lay.bytes // lay.elem_bytes
+        self.fields = [torch.empty(n, dtype=dtype, device=self.device) for _ in range(2)]
+        self.ncoef = NCOEF[self.kind]
+        self.coefs = []
+        if self.ncoef:
+            cl = self._layout(C.STENCIL_COEF_ARRAY)
+            self.coefs = [torch.empty(cl.bytes // cl.elem_bytes, dtype=self.coef_dtype, device=self.device)
+                          for _ in range(self.ncoef)]
+        wsb = int(C.lib().stencil_workspace_bytes(self._h))
+        self.workspace = torch.empty(max(wsb, 16), dtype=torch.uint8, device=self.device) if wsb else None
+        carr = (ctypes.c_void_p * 13)(*[c.data_ptr() for c in self.coefs])
+        C.call("stencil_bind", self._h, _ptr(self.fields[0]), _ptr(self.fields[1]),
+               carr if self.ncoef else None,
+               _ptr(self.workspace) if self.workspace is not None else None)
+
+    # ------------------------------------------------------------ layout
+    def _layout(self, which) -> C.stencil_layout:
+        out = C.stencil_layout()
+        C.call("stencil_layout_of", self._h, which, ctypes.byref(out))
+        return out
+
+    def padded(self, t: torch.Tensor) -> torch.Tensor:
+        lay = self.layout
+        return t.view(lay.planes, lay.pitch_y, lay.pitch_x)
+
+    def interior(self, t: torch.Tensor) -> torch.Tensor:
+        lay = self.layout
+        r, xo = lay.radius, lay.x_offset
+        return self.padded(t)[r:r + self.nz, r:r + self.ny, xo:xo + self.nx]
+
+    @property
+    def parity(self) -> int:
+        return C.call("stencil_parity", self._h)
+
+    @property
+    def current(self) -> torch.Tensor:
+        """Interior view (no copy) of the array holding the current time level."""
+        return self.interior(self.fields[self.parity])
+
+    # ------------------------------------------------------------ data
+    def set_coeffs(self, scalars=None, arrays=None):
+        if self.kind == C.STENCIL_7PT_CONST:
+            sc = (ctypes.c_double * 2)(*[float(v) for v in scalars])
+            C.call("stencil_set_coeffs", self._h, sc, None, C.STENCIL_HOST)
+            return
+        arrs = [a.to(self.coef_dtype).contiguous() for a in arrays]
+        assert len(arrs) == self.ncoef
+        for a in arrs:
+            assert tuple(a.shape) == (self.nz, self.ny, self.nx), a.shape
+        where = C.STENCIL_HOST if arrs[0].device.type == "cpu" else C.STENCIL_DEVICE
+        ptrs = (ctypes.c_void_p * self.ncoef)(*[a.data_ptr() for a in arrs])
+        C.call("stencil_set_coeffs", self._h, None, ptrs, where)
+        if where == C.STENCIL_HOST:
+            self.sync()
+        self._keep = arrs  # device sources stay alive until the copies are done
+
+    def set_field(self, u0: torch.Tensor, halo: float = 0.0):
+        u = u0.to(self.dtype).contiguous()
+        assert tuple(u.shape) == (self.nz, self.ny, self.nx), u.shape
+        where = C.STENCIL_HOST if u.device.type == "cpu" else C.STENCIL_DEVICE
+        C.call("stencil_set_field", self._h, _ptr(u), float(halo), where)
+        if where == C.STENCIL_HOST:
+            self.sync()
+        self._keep_u = u
+
+    def get_field(self, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Dense interior copy of the current field (into ``out`` if given; host or device)."""
+        if out is None:
+            out = torch.empty((self.nz, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        assert out.is_contiguous() and out.dtype == self.dtype
+        where = C.STENCIL_HOST if out.device.type == "cpu" else C.STENCIL_DEVICE
+        C.call("stencil_get_field", self._h, _ptr(out), where)
+        return out
+
+    # ------------------------------------------------------------ schedule
+    def set_tuning(self, scheme: str = "plain", tuning: Tuning | None = None):
+        t = tuning.c() if tuning is not None else None
+        C.call("stencil_set_tuning", self._h, SCHEMES[scheme], ctypes.byref(t) if t is not None else None)
+
+    def blocked_smem_bytes(self, tuning: Tuning) -> int:
+        t = tuning.c()
+        return int(C.lib().stencil_blocked_smem_bytes(self._h, ctypes.byref(t)))
+
+    def run(self, T: int):
+        C.call("stencil_run", self._h, int(T))
+
+    def sync(self):
+        C.call("stencil_sync", self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            C.lib().stencil_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

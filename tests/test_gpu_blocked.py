@@ -1,0 +1,102 @@
+"""Temporally blocked (diamond / wavefront) sweeps on the GPU.
+
+The blocked kernel evaluates every update with the same device function and the
+same operand values as the plain sweep, so the two must agree bit for bit on
+any shape, step count and tuning; that is the sharpest detector of tiling
+mistakes (a wrong parity array, a missing boundary row, a stale ring slot).
+Oracle parity of the blocked path is checked as well.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_5561_gb300.stencil import Tuning
+from tests._util import Problem, step_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(p, T, scheme, tuning=None):
+    s = p.make()
+    s.set_tuning(scheme, tuning)
+    s.run(T)
+    return s.get_field().cpu().numpy()
+
+
+R1_TUNINGS = [Tuning(4, 1, 4, 1), Tuning(8, 1, 8, 2), Tuning(8, 2, 8, 3), Tuning(16, 1, 16, 4),
+              Tuning(12, 3, 4, 1), Tuning(2, 1, 2, 1), Tuning(24, 1, 8, 2)]
+R4_TUNINGS = [Tuning(8, 1, 8, 1), Tuning(16, 1, 8, 2), Tuning(16, 2, 16, 3), Tuning(32, 1, 8, 4)]
+
+
+@pytest.mark.parametrize("tn", R1_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xsplit}")
+@pytest.mark.parametrize("kind,shape,fdt,cdt", [
+    ("7pt_const", (45, 37, 23), "f32", None),
+    ("7pt_var", (33, 29, 19), "f32", None),
+    ("7pt_var", (40, 13, 17), "f32", "bf16"),
+    ("7pt_const", (30, 21, 12), "f64", None),
+])
+@pytest.mark.parametrize("T", [1, 6, 13])
+def test_blocked_bitwise_equals_plain_r1(kind, shape, fdt, cdt, tn, T):
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=11, halo=0.125)
+    a = _run(p, T, "plain")
+    b = _run(p, T, "blocked", tn)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("tn", R4_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xsplit}")
+@pytest.mark.parametrize("shape,fdt", [((29, 35, 21), "f32"), ((18, 25, 14), "f64")])
+@pytest.mark.parametrize("T", [1, 5, 9])
+def test_blocked_bitwise_equals_plain_r4(shape, fdt, tn, T):
+    p = Problem("25pt_var", *shape, fdt=fdt, seed=12, halo=-0.25)
+    a = _run(p, T, "plain")
+    b = _run(p, T, "blocked", tn)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("kind,shape,fdt,T,tn", [
+    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(8, 1, 8, 1)),
+    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(16, 2, 8, 2)),
+    ("7pt_var", (50, 47, 31), "f32", 10, Tuning(8, 1, 8, 2)),
+    ("25pt_var", (40, 33, 30), "f32", 6, Tuning(16, 1, 8, 2)),
+])
+def test_blocked_matches_oracle(kind, shape, fdt, T, tn):
+    p = Problem(kind, *shape, fdt=fdt, seed=13)
+    got = _run(p, T, "blocked", tn).astype(np.float64)
+    ref = p.oracle(T)
+    assert oracle.step_normalised_l2(got, ref, T) <= step_tol(fdt)
+    assert np.max(np.abs(got - ref)) <= p.elementwise_tol(T)
+
+
+def test_blocked_small_and_degenerate_shapes():
+    for shape in [(1, 1, 1), (5, 2, 3), (9, 3, 40), (64, 1, 5), (3, 70, 2)]:
+        p = Problem("7pt_var", *shape, fdt="f32", seed=14, halo=0.5)
+        for tn in [Tuning(4, 1, 4, 1), Tuning(8, 2, 8, 2)]:
+            a = _run(p, 7, "plain")
+            b = _run(p, 7, "blocked", tn)
+            assert np.array_equal(a, b), (shape, tn)
+
+
+def test_blocked_successive_runs_and_parity():
+    p = Problem("7pt_const", 40, 40, 40, fdt="f32", seed=15)
+    s = p.make()
+    s.set_tuning("blocked", Tuning(8, 1, 8, 2))
+    s.run(3)
+    s.run(4)
+    s.run(0)
+    s.run(6)
+    a = s.get_field().cpu().numpy()
+    assert s.parity == 13 % 2
+    b = _run(p, 13, "plain")
+    assert np.array_equal(a, b)
+
+
+def test_infeasible_tuning_rejected():
+    from paper_1410_5561_gb300._lib import StencilError
+    p = Problem("7pt_const", 64, 64, 64, fdt="f32", seed=1)
+    s = p.make()
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(7, 1, 8, 1))    # D_w not a multiple of 2R
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(64, 8, 8, 1))   # rings far beyond shared memory
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(8, 1, 8, 17))   # cluster too large

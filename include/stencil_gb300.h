@@ -64,15 +64,16 @@ enum stencil_status {
 };
 
 /* Blocked-schedule tunables (Section II-A, III-A): dw = diamond width D_w
- * along y (a multiple of 2R), nf = frontlines N_F (z planes per time level per
- * wavefront step), warps = warps per CTA, xsplit = CTAs per thread-block
- * cluster; the cluster is the thread group that shares one extruded diamond,
- * its CTAs splitting x (1..16). */
+ * along y (a multiple of 2R, at most 64R), nf = frontlines N_F (z planes per
+ * time level per wavefront step, 1..16), warps = warps per CTA (1..16; the
+ * CTA is the thread group that shares one extruded diamond), xtile = x columns
+ * one CTA owns (a multiple of 16 bytes' worth of field elements; the leading-
+ * dimension tile of Section III-A). */
 typedef struct {
     int dw;
     int nf;
     int warps;
-    int xsplit;
+    int xtile;
 } stencil_tuning;
 
 typedef struct {
@@ -139,6 +140,15 @@ int stencil_get_field(stencil_t h, void* dst, int where);
 /* Shared-memory bytes per CTA the blocked kernel needs for a tuning (0 if the
  * tuning is malformed); the device limit is cudaDevAttrMaxSharedMemoryPerBlockOptin. */
 size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning);
+
+/* Number of kernels this handle has launched so far (sweeps, fills), into *out. */
+int stencil_launch_count(stencil_t h, long long* out);
+
+/* Measurement support, no counterpart in the paper: time a grid-filling kernel
+ * of independent dependent-FMA chains in dtype (STENCIL_F32 or STENCIL_F64) on
+ * cuda_stream and return its duration (*seconds) and flop count (*flops, two
+ * per FMA). scratch: device buffer of at least 65536 bytes. Synchronous. */
+int stencil_probe_fma(int dtype, int iters, void* scratch, void* cuda_stream, double* seconds, double* flops);
 
 /* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error. */
 int stencil_sync(stencil_t h);

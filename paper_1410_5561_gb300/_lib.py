@@ -24,7 +24,7 @@ STATUS = {0: "STENCIL_OK", -1: "STENCIL_EINVAL", -2: "STENCIL_ENOSMEM", -3: "STE
 
 class stencil_tuning(ctypes.Structure):
     _fields_ = [("dw", ctypes.c_int), ("nf", ctypes.c_int), ("warps", ctypes.c_int),
-                ("xsplit", ctypes.c_int)]
+                ("xtile", ctypes.c_int)]
 
 
 class stencil_layout(ctypes.Structure):
@@ -59,6 +59,9 @@ SIGNATURES = [
     ("stencil_parity", _I, [_H]),
     ("stencil_get_field", _I, [_H, _P, _I]),
     ("stencil_blocked_smem_bytes", ctypes.c_size_t, [_H, ctypes.POINTER(stencil_tuning)]),
+    ("stencil_launch_count", _I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    ("stencil_probe_fma", _I, [_I, _I, _P, _P, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]),
     ("stencil_sync", _I, [_H]),
     ("stencil_strerror", ctypes.c_char_p, [_I]),
     ("stencil_destroy", _I, [_H]),

@@ -23,6 +23,7 @@ struct stencil_grid {
     int scheme;
     BlockedTune tune;
     bool tune_set;
+    long long launches;
 };
 
 static int from_cuda(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
@@ -42,20 +43,23 @@ static SweepArgs args_of(const stencil_grid* h) {
     return a;
 }
 
-// Default blocked tuning: D_w = 8 (R = 1) or 16 (R = 4), one frontline, 8 warps,
-// x split so that each CTA holds at most 128 FP32 (64 FP64) columns; D_w is
-// halved until the rings fit the shared-memory opt-in limit.
+// Default blocked tuning: D_w = 8 (R = 1) or 16 (R = 4), one frontline, 16 (8)
+// warps, x tiles sized so that a tile row plus its trapezoid overlap is one warp
+// of vectors; D_w is halved until the rings fit the shared-memory opt-in limit.
 static BlockedTune default_tune(const stencil_grid* h) {
     BlockedTune t{};
     int R = kind_radius(h->kind);
     int eb = dtype_bytes(h->fdt);
-    int maxcols = 512 / eb;
     t.dw = R == 1 ? 8 : 16;
     t.nf = 1;
-    t.warps = 8;
-    t.cx = (h->L.nx + maxcols - 1) / maxcols;
-    if (t.cx < 1) t.cx = 1;
-    if (t.cx > 16) t.cx = 16;
+    t.warps = R == 1 ? 16 : 8;
+    {
+        // widest x tile whose bottom level (tile plus trapezoid overlap) fits one warp of vectors
+        int V = 16 / eb;
+        int ov = ((R * (t.dw / R - 2) + V - 1) / V) * V;
+        t.xtile = 32 * V - 2 * ov;
+        if (t.xtile < V) t.xtile = V;
+    }
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 0;
@@ -118,6 +122,7 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
     h->parity = 0;
     h->scheme = STENCIL_PLAIN;
     h->tune_set = false;
+    h->launches = 0;
     *out = h;
     return STENCIL_OK;
 }
@@ -193,6 +198,7 @@ int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* ar
         if (!arrays[m]) return STENCIL_EINVAL;
         cudaError_t e = fill_value(h->coef[m], h->L.count(), h->cdt, 0.0, h->stream);
         if (e != cudaSuccess) return STENCIL_ECUDA;
+        ++h->launches;
         e = copy_interior(h, eb, arrays[m], h->coef[m], true);
         if (e != cudaSuccess) return STENCIL_ECUDA;
     }
@@ -206,6 +212,7 @@ int stencil_set_field(stencil_t h, const void* src, double halo_value, int where
     for (int i = 0; i < 2; ++i) {
         cudaError_t e = fill_value(h->field[i], h->L.count(), h->fdt, halo_value, h->stream);
         if (e != cudaSuccess) return STENCIL_ECUDA;
+        ++h->launches;
     }
     cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), src, h->field[0], true);
     if (e != cudaSuccess) return STENCIL_ECUDA;
@@ -226,7 +233,7 @@ int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning) {
         t.dw = tuning->dw;
         t.nf = tuning->nf;
         t.warps = tuning->warps;
-        t.cx = tuning->xsplit;
+        t.xtile = tuning->xtile;
     }
     int rc = check_tune(h, t);
     if (rc != STENCIL_OK) {
@@ -248,7 +255,7 @@ int stencil_run(stencil_t h, int T) {
     if (T == 0) return STENCIL_OK;
     SweepArgs a = args_of(h);
     if (h->scheme == STENCIL_BLOCKED) {
-        cudaError_t e = blocked_run(a, h->field, h->parity, T, h->tune, h->stream);
+        cudaError_t e = blocked_run(a, h->field, h->parity, T, h->tune, h->stream, &h->launches);
         if (e == cudaErrorInvalidValue) return STENCIL_EINVAL;
         if (e != cudaSuccess) return STENCIL_ECUDA;
     } else {
@@ -256,6 +263,7 @@ int stencil_run(stencil_t h, int T) {
             int p = (h->parity + t) & 1;
             cudaError_t e = plain_step(a, h->field[p], h->field[p ^ 1], h->stream);
             if (e != cudaSuccess) return STENCIL_ECUDA;
+            ++h->launches;
         }
     }
     h->parity = (h->parity + T) & 1;
@@ -276,8 +284,14 @@ int stencil_get_field(stencil_t h, void* dst, int where) {
 
 size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning) {
     if (!h || !tuning) return 0;
-    BlockedTune t{tuning->dw, tuning->nf, tuning->warps, tuning->xsplit};
+    BlockedTune t{tuning->dw, tuning->nf, tuning->warps, tuning->xtile};
     return blocked_smem_bytes(args_of(h), t);
+}
+
+int stencil_launch_count(stencil_t h, long long* out) {
+    if (!h || !out) return STENCIL_EINVAL;
+    *out = h->launches;
+    return STENCIL_OK;
 }
 
 int stencil_sync(stencil_t h) {

@@ -1,52 +1,62 @@
 // Temporally blocked sweep: diamond tiling in (y, t), wavefront along z,
-// x split across the CTAs of a thread-block cluster.
+// overlapped (trapezoidal) tiles along x.
 //
 // Paper: Section II-A (multicore wavefront diamond blocking, MWD): extruded
 // diamonds in the (y, t) plane, traversed as a wavefront along z, with a group
 // of threads sharing one cache block; "frontlines" N_F planes per level per
-// wavefront step; Section III-A (leading-dimension tiling). The GPU version:
+// wavefront step; Section III-A (tiling of the leading dimension). The GPU
+// version:
 //
 // * Tile geometry. With slope R per step and width D (a multiple of 2R),
 //   update (y, t) (producing u_{t+1}(y)) belongs to tile (a, b) with
 //   a = floor((y + R t) / D), b = floor((y - R t) / D). Row k = a - b holds
 //   tiles that are mutually independent; tile (k, b) depends on (k-1, b) and
-//   (k-1, b+1). Each row advances D/(2R) steps on average (Eq. 5's volume
-//   N_z D^2 / (2R)). Rows run as successive launches on one stream, which is
-//   the GPU counterpart of the paper's FIFO queue of ready diamonds.
-// * One cluster of CX CTAs processes one tile for all z (the paper's thread
-//   group). CTA c owns x in [c*Xt, (c+1)*Xt) and pushes its edge vectors into
-//   its neighbours' rings through distributed shared memory.
-// * Each time level l of the tile keeps a ring of Q = 2(N_F + R) planes in
-//   shared memory holding u_{t_l} on rows N_l = Yc(t_l) +- R. Level l computes
-//   planes [s N_F - l d, s N_F - l d + N_F) at step s with d = N_F + R, so all
-//   levels of one step are independent and one cluster barrier per step
-//   suffices.
+//   (k-1, b+1). Each row advances D/(2R) steps on average (the diamond volume
+//   N_z D^2 / (2R) of Section III-C). Rows run as successive launches on one
+//   stream: the GPU counterpart of the paper's FIFO queue of ready diamonds.
+// * One CTA (the thread group) processes one tile for one x-tile and all z.
+//   Along x the CTA computes a trapezoid: level l covers R*(Lt-1-l) extra
+//   columns on each side, so x-tiles exchange no data. The x-tiles of one
+//   diamond run as one thread-block cluster that advances in lockstep (an
+//   execution-only barrier per step), which orders a neighbour's HBM store
+//   after the loads of the same (parity-array) cells in its overlap.
+// * Each time level l keeps a ring of Q = 3 N_F + 2R planes in shared memory
+//   holding u_{t_l} on rows N_l = Yc(t_l) +- R. Level l computes planes
+//   [s N_F - l d, s N_F - l d + N_F) at step s with d = N_F + R, so the levels
+//   of one step are independent and one __syncthreads per step suffices.
+//   Boundary rows are prefetched one step ahead with cp.async.
+// * Every warp owns a fixed set of (level, row) items for the whole sweep; for
+//   the radius-1 stencils it keeps the item's z-window in registers across
+//   steps, so each plane costs one shared-memory load of the new plane, the
+//   y-neighbour loads and a few shuffles for the x-neighbours.
 // * HBM traffic is only the diamond boundary (Section III-C): rows of N_l not
-//   computed by level l-1 are loaded from array (p0 + t_l) & 1 with cp.async;
-//   an update is stored to array (p0 + t + 1) & 1 only if a point of another
-//   tile reads it (or t = T-1). Coefficients are read through L2.
+//   computed by level l-1 are loaded from array (p0 + t_l) & 1; an update is
+//   stored to array (p0 + t + 1) & 1 only if a point of another tile reads it
+//   (or t = T-1). Coefficients are read through L2.
 // * The per-point arithmetic is the shared update of common.cuh, so results
 //   are bit-identical to the plain sweep.
-#include <cooperative_groups.h>
-
 #include "internal.h"
-
-namespace cg = cooperative_groups;
 
 namespace stg {
 
-constexpr int MAXLV = 64;        // levels per tile (D/R - 1 <= 63)
+constexpr int MAXLV = 64;        // levels per tile (D/R - 1 <= 64)
+constexpr int MAXTASK = 256;     // HBM-load / fill row tasks per tile
+constexpr int MAXITEM = 256;     // computed rows per tile (one warp-wide chunk each)
 constexpr int BLK_MAXT = 512;    // threads per CTA
+constexpr int MAXCLUSTER = 16;   // x-tiles of one diamond run as one cluster
 
 struct TileMeta {
-    int Lt, t0;
+    int Lt, t0, ntask, nitem;
     int clo[MAXLV], chi[MAXLV];        // computed rows (interior), empty: clo == chi
     int nlo[MAXLV], nhi[MAXLV];        // ring rows [nlo, nhi) in [-R, Ny + R)
-    int l0lo[MAXLV], l0hi[MAXLV];      // interior rows loaded from HBM, interval 0
-    int l1lo[MAXLV], l1hi[MAXLV];      // interval 1
     int wlo[MAXLV], whi[MAXLV];        // computed rows NOT stored to HBM
     int roff[MAXLV];                   // ring element offset in shared memory
-    int ipre[MAXLV + 1];               // prefix sums of computed rows
+    int vlo[MAXLV];                    // first computed ring vector
+    int xlo[MAXLV], xhi[MAXLV];        // computed x range (interior coordinates)
+    int ldlo[MAXLV], ldhi[MAXLV];      // ring vectors loaded for this level's input
+    short tl[MAXTASK], ty[MAXTASK];    // load / fill tasks for interior planes
+    unsigned char tfill[MAXTASK];
+    short il[MAXITEM], iy[MAXITEM];    // compute items (level, row)
 };
 
 template <typename TF, typename TC>
@@ -55,7 +65,7 @@ struct BlkParams {
     TF* f[2];
     const TC* C[13];
     TF c0, c1, halo;
-    int p0, T, D, NF, row, bmin, Xt, CX, Q, Xs;
+    int p0, T, D, row, bmin, Xt, EH, Q, Xs, CX;
 };
 
 __host__ __device__ inline void level_rows(int D, int R, int Ny, int a, int b, int t, int& lo, int& hi) {
@@ -80,20 +90,51 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Execution-only barrier across the cluster (the x-tiles of one diamond). It
+// carries no memory ordering: it only keeps the x-tiles in lockstep so that a
+// neighbour's HBM store of step s lands after this CTA's cp.async loads issued
+// at step s-2 or earlier have completed (their wait_group precedes the arrive).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ int pmod(int a, int q) {
     int r = a % q;
     return r < 0 ? r + q : r;
 }
+__device__ __forceinline__ int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__device__ __forceinline__ int cdiv(int a, int b) { return -fdiv(-a, b); }
+__device__ __forceinline__ int wrap_inc(int s, int q) { return s + 1 == q ? 0 : s + 1; }
 
-template <int KIND, typename TF, typename TC>
+// Per-warp state of one owned item (level l, row y): pointers and lane flags.
+template <typename TF, int V>
+struct Item {
+    const TF* rowp;   // ring row y of level l, slot 0, this lane's vector
+    TF* dstp;         // ring row y of level l+1, slot 0, this lane's vector (or null)
+    TF* gdst;         // HBM array receiving u_{t+1}
+    size_t g0;        // element index of (xg, y, z = 0)
+    int PS, dPS;      // ring plane strides (elements)
+    int zb0;          // z of the item's first plane at step 0 (= -l d)
+    int qr;           // vectors available to the right of this lane's vector
+    int xg;           // interior x of the lane's element 0
+    int wz;           // plane the register window is positioned at (-inf: reload)
+    bool valid, active, indom, full, store;
+};
+
+template <int KIND, typename TF, typename TC, int K, int NF>
 __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF, TC> P) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int NC = KindTraits<KIND>::NC;
     constexpr int V = 16 / sizeof(TF);
     constexpr int J = (R + V - 1) / V;
     constexpr int HV = J * V;
+    constexpr bool PERSIST = (R == 1);  // keep z-windows in registers across steps
+    constexpr int WIN = 2 * R + NF;
     using VT = Vec<TF, V>;
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -105,15 +146,15 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
     const int NT = blockDim.x;
     const int NW = NT >> 5;
     const int warp = tid >> 5, lane = tid & 31;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int crank = P.CX > 1 ? (int)cluster.block_rank() : 0;
     const int k = P.row;
     const int b = P.bmin + (int)blockIdx.y;
     const int a = b + k;
-    const int D = P.D, NF = P.NF, Q = P.Q, Xs = P.Xs, Xt = P.Xt;
-    const int d = NF + R;
-    const int x0 = crank * Xt;
+    const int D = P.D, Q = P.Q, Xs = P.Xs, Xt = P.Xt, EH = P.EH;
+    constexpr int d = NF + R;
+    const int x0 = (int)blockIdx.x * Xt;
     const int Ny = L.ny, Nz = L.nz, Nx = L.nx;
+    const int rnx = ((Nx + V - 1) / V) * V;
+    const int nvs = Xs / V;  // vectors per ring row
 
     if (tid == 0) {
         int tlo, thi;
@@ -122,14 +163,12 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
         if (Lt > MAXLV) Lt = MAXLV;  // host guarantees D/R - 1 <= MAXLV
         M.Lt = Lt;
         M.t0 = tlo;
-        int off = 0;
-        M.ipre[0] = 0;
+        int off = 0, ntask = 0, nitem = 0;
         for (int l = 0; l < Lt; ++l) {
             int lo, hi;
             level_rows(D, R, Ny, a, b, tlo + l, lo, hi);
             M.clo[l] = lo;
             M.chi[l] = hi;
-            M.ipre[l + 1] = M.ipre[l] + (hi - lo);
             int nlo = 0, nhi = 0;
             if (hi > lo) {
                 nlo = lo - R;
@@ -139,28 +178,49 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
             M.nhi[l] = nhi;
             M.roff[l] = off;
             off += Q * (nhi - nlo) * Xs;
-            // interior rows of N_l that level l-1 does not compute
-            int alo = nlo < 0 ? 0 : nlo, ahi = nhi > Ny ? Ny : nhi;
-            if (ahi < alo) ahi = alo;
-            int blo = 1 << 30, bhi = 1 << 30;
-            if (l > 0 && M.chi[l - 1] > M.clo[l - 1]) {
-                blo = M.clo[l - 1];
-                bhi = M.chi[l - 1];
+            // x extent: level l computes [x0 - e, x0 + Xt + e), e = R (Lt - 1 - l),
+            // clipped to [-HV, rnx + HV); its input spans R more on each side.
+            const int e = R * (Lt - 1 - l);
+            int xl = x0 - e, xh = x0 + Xt + e;
+            if (xl < -HV) xl = -HV;
+            if (xh > rnx + HV) xh = rnx + HV;
+            M.xlo[l] = xl;
+            M.xhi[l] = xh;
+            M.vlo[l] = fdiv(xl - x0 + EH, V);
+            int il_ = x0 - e - R, ih_ = x0 + Xt + e + R;
+            if (il_ < -HV) il_ = -HV;
+            if (ih_ > rnx + HV) ih_ = rnx + HV;
+            M.ldlo[l] = fdiv(il_ - x0 + EH, V);
+            M.ldhi[l] = cdiv(ih_ - x0 + EH, V);
+            // load tasks: interior rows of N_l that level l-1 does not compute, and halo rows
+            if (hi > lo) {
+                const bool prev = l > 0 && M.chi[l - 1] > M.clo[l - 1];
+                const int blo = prev ? M.clo[l - 1] : 1 << 30, bhi = prev ? M.chi[l - 1] : 1 << 30;
+                for (int y = nlo; y < nhi; ++y) {
+                    const bool halo_row = y < 0 || y >= Ny;
+                    const bool computed = !halo_row && y >= blo && y < bhi;
+                    if (computed || ntask >= MAXTASK) continue;
+                    M.tl[ntask] = (short)l;
+                    M.ty[ntask] = (short)y;
+                    M.tfill[ntask] = halo_row ? 1 : 0;
+                    ++ntask;
+                }
+                for (int y = lo; y < hi && nitem < MAXITEM; ++y) {
+                    M.il[nitem] = (short)l;
+                    M.iy[nitem] = (short)y;
+                    ++nitem;
+                }
             }
-            M.l0lo[l] = alo;
-            M.l0hi[l] = ahi < blo ? ahi : blo;
-            if (M.l0hi[l] < M.l0lo[l]) M.l0hi[l] = M.l0lo[l];
-            M.l1lo[l] = alo > bhi ? alo : bhi;
-            M.l1hi[l] = ahi;
-            if (M.l1hi[l] < M.l1lo[l]) M.l1hi[l] = M.l1lo[l];
         }
+        M.ntask = ntask;
+        M.nitem = nitem;
         for (int l = 0; l < Lt; ++l) {
-            int t = tlo + l;
-            bool all = (t == P.T - 1) || (l + 1 >= Lt) || (M.chi[l + 1] <= M.clo[l + 1]);
+            const int t = tlo + l;
+            const bool all = (t == P.T - 1) || (l + 1 >= Lt) || (M.chi[l + 1] <= M.clo[l + 1]);
             if (all) {
                 M.wlo[l] = M.whi[l] = 0;
             } else {
-                int c2lo = M.clo[l + 1], c2hi = M.chi[l + 1];
+                const int c2lo = M.clo[l + 1], c2hi = M.chi[l + 1];
                 M.wlo[l] = c2lo > 0 ? c2lo + R : 0;
                 M.whi[l] = c2hi < Ny ? c2hi - R : Ny;
                 if (M.whi[l] < M.wlo[l]) M.whi[l] = M.wlo[l];
@@ -169,141 +229,159 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
     }
     __syncthreads();
     const int Lt = M.Lt;
-    const TF hv = P.halo;
-
-    // Outer x-halo columns of the cluster's end CTAs hold the Dirichlet value for good.
-    if (crank == 0 || crank == P.CX - 1) {
-        int totrows = 0;
-        for (int l = 0; l < Lt; ++l) totrows += Q * (M.nhi[l] - M.nlo[l]);
-        for (int i = tid; i < totrows * (2 * HV); i += NT) {
-            int r = i / (2 * HV), c = i % (2 * HV);
-            int col = c < HV ? c : Xt + c;  // [0,HV) or [HV+Xt, Xs)
-            if ((c < HV && crank == 0) || (c >= HV && crank == P.CX - 1)) ring[(size_t)r * Xs + col] = hv;
-        }
-    }
-    if (P.CX > 1) cluster.sync(); else __syncthreads();
     if (Lt == 0) return;
-
-    // Work decomposition for the compute phase: G lanes per row (one vector each).
-    const int G = Xt / V;
-    const int nslots = NT / G;
-    const int slot = tid / G;
-    const int xv = tid - slot * G;
-    const int xg = x0 + xv * V;  // interior x of this lane's vector element 0
-    const int totitems = M.ipre[Lt];
-
+    const TF hv = P.halo;
+    const int ntask = M.ntask;
     const int s_begin = -((2 * R + NF + NF - 1) / NF);
     const int s_end = (Nz - 1 + (Lt - 1) * d) / NF + 1;
+    const size_t gplane = L.plane();
 
-    // global vector range to load: [x0 - HV, min(x0 + Xt + HV, roundup(Nx, V) + HV))
-    const int xend = ((Nx + V - 1) / V) * V + HV;
-    const int lv_hi = (min(x0 + Xt + HV, xend) - (x0 - HV)) / V;  // vectors per loaded row
-
-    for (int s = s_begin; s < s_end; ++s) {
-        // ---------------- producer: HBM loads and Dirichlet fills (one warp per row)
-        {
-            int g = 0;
-            for (int l = 0; l < Lt; ++l) {
-                const int nlo = M.nlo[l], nhi = M.nhi[l];
-                if (nhi <= nlo) continue;
-                const int nrows = nhi - nlo;
-                TF* rb = ring + M.roff[l];
-                const TF* src = P.f[(P.p0 + M.t0 + l) & 1];
-                const int zb = s * NF - l * d + NF + R;
-                for (int f = 0; f < NF; ++f) {
-                    const int z = zb + f;
-                    if (z < -R || z >= Nz + R) continue;
-                    const bool hplane = (z < 0 || z >= Nz);
-                    const int n0 = M.l0hi[l] - M.l0lo[l], n1 = M.l1hi[l] - M.l1lo[l];
-                    const int hlo = nlo < 0 ? -nlo : 0;            // halo rows below 0: [nlo, 0)
-                    const int hhi = nhi > Ny ? nhi - Ny : 0;       // halo rows at/after Ny
-                    const int cnt = hplane ? nrows : (n0 + n1 + hlo + hhi);
-                    TF* slotb = rb + (size_t)pmod(z, Q) * nrows * Xs;
-                    int i0 = pmod(warp - g, NW);
-                    for (int i = i0; i < cnt; i += NW) {
-                        int y;
-                        bool fill;
-                        if (hplane) {
-                            y = nlo + i;
-                            fill = true;
-                        } else if (i < n0) {
-                            y = M.l0lo[l] + i;
-                            fill = false;
-                        } else if (i < n0 + n1) {
-                            y = M.l1lo[l] + (i - n0);
-                            fill = false;
-                        } else if (i < n0 + n1 + hlo) {
-                            y = nlo + (i - n0 - n1);
-                            fill = true;
-                        } else {
-                            y = Ny + (i - n0 - n1 - hlo);
-                            fill = true;
-                        }
-                        TF* rowp = slotb + (size_t)(y - nlo) * Xs;
-                        if (fill) {
-                            VT hvv;
+    // ---- per-warp owned items
+    Item<TF, V> it[K];
+    VT win[K][WIN];
 #pragma unroll
-                            for (int e = 0; e < V; ++e) hvv.v[e] = hv;
-                            for (int c = lane; c < Xs / V; c += 32) stv<TF, V>(rowp + c * V, hvv);
-                        } else {
-                            const TF* gp = src + L.at(x0 - HV, y, z);
-                            for (int c = lane; c < lv_hi; c += 32) cp_async16(rowp + c * V, gp + c * V);
-                        }
-                    }
-                    g += cnt;
+    for (int kk = 0; kk < K; ++kk) {
+        Item<TF, V>& I = it[kk];
+        const int id = warp + kk * NW;
+        I.valid = id < M.nitem;
+        I.wz = -(1 << 30);
+        if (!I.valid) continue;
+        const int l = M.il[id], y = M.iy[id];
+        const int nlo = M.nlo[l];
+        I.PS = (M.nhi[l] - nlo) * Xs;
+        const int v = M.vlo[l] + lane;
+        const int vr = v < nvs ? v : nvs - 1;  // clamped read vector (inactive lanes only)
+        I.qr = nvs - 1 - vr;
+        I.rowp = ring + M.roff[l] + (y - nlo) * Xs + vr * V;
+        I.xg = x0 - EH + v * V;
+        I.active = (I.xg + V > M.xlo[l]) && (I.xg < M.xhi[l]);
+        I.indom = I.xg >= 0 && I.xg < Nx;
+        I.full = I.xg >= 0 && I.xg + V <= Nx;
+        I.dstp = nullptr;
+        I.dPS = 0;
+        if (l + 1 < Lt && y >= M.nlo[l + 1] && y < M.nhi[l + 1]) {
+            I.dstp = ring + M.roff[l + 1] + (y - M.nlo[l + 1]) * Xs + v * V;
+            I.dPS = (M.nhi[l + 1] - M.nlo[l + 1]) * Xs;
+        }
+        I.store = I.active && I.indom && !(y >= M.wlo[l] && y < M.whi[l]) && I.xg >= x0 && I.xg < x0 + Xt;
+        I.g0 = I.indom ? L.at(I.xg, y, 0) : 0;
+        I.gdst = P.f[(P.p0 + M.t0 + l + 1) & 1];
+        I.zb0 = -l * d;
+    }
+
+    // ---- producer: HBM loads (cp.async) and Dirichlet fills of planes P_l(s) = [s NF - l d + NF + R, +NF)
+    auto produce = [&](int s) {
+        VT hvv;
+#pragma unroll
+        for (int e = 0; e < V; ++e) hvv.v[e] = hv;
+        for (int ti = warp; ti < ntask; ti += NW) {
+            const int l = M.tl[ti], y = M.ty[ti];
+            const bool fill = M.tfill[ti] != 0;
+            const int nlo = M.nlo[l];
+            const int PS = (M.nhi[l] - nlo) * Xs;
+            TF* rowr = ring + M.roff[l] + (y - nlo) * Xs;
+            const int ldlo = M.ldlo[l], ldhi = M.ldhi[l];
+            const int zb = s * NF - l * d + NF + R;
+            const TF* src = fill ? nullptr : P.f[(P.p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH);
+#pragma unroll
+            for (int fz = 0; fz < NF; ++fz) {
+                const int z = zb + fz;
+                if (z < 0 || z >= Nz) continue;
+                TF* dst = rowr + pmod(z, Q) * PS;
+                if (fill) {
+                    for (int c = ldlo + lane; c < ldhi; c += 32) stv<TF, V>(dst + c * V, hvv);
+                } else {
+                    const TF* gp = src + (size_t)z * gplane;
+                    for (int c = ldlo + lane; c < ldhi; c += 32) cp_async16(dst + c * V, gp + c * V);
                 }
             }
         }
-        // ---------------- compute: items (level, row), N_F planes each
-        if (slot < nslots) {
-            int l = 0;
-            for (int it = slot; it < totitems; it += nslots) {
-                while (it >= M.ipre[l + 1]) ++l;
-                const int y = M.clo[l] + (it - M.ipre[l]);
-                const int zb = s * NF - l * d;
-                if (zb + NF <= 0 || zb >= Nz) continue;
-                const int nlo = M.nlo[l];
-                const int nrows = M.nhi[l] - nlo;
-                const TF* rb = ring + M.roff[l];
-                const int t = M.t0 + l;
-                // destination ring (level l+1), if it holds row y
-                TF* rdst = nullptr;
-                int dnlo = 0, dnrows = 0;
-                if (l + 1 < Lt && y >= M.nlo[l + 1] && y < M.nhi[l + 1]) {
-                    rdst = ring + M.roff[l + 1];
-                    dnlo = M.nlo[l + 1];
-                    dnrows = M.nhi[l + 1] - dnlo;
-                }
-                const bool store = !(y >= M.wlo[l] && y < M.whi[l]);
-                TF* gdst = P.f[(P.p0 + t + 1) & 1];
-                auto at = [&](int z, int yy, int col) -> const TF* {
-                    return rb + ((size_t)pmod(z, Q) * nrows + (yy - nlo)) * Xs + col;
-                };
-                const int col = HV + xv * V;
-                VT zr[2 * R + 1];
-                const int zfirst = zb < 0 ? 0 : zb;
-                const int zlast = (zb + NF < Nz ? zb + NF : Nz);
+        // Dirichlet z-halo planes: every row of the level's ring
+        for (int l = 0; l < Lt; ++l) {
+            const int zb = s * NF - l * d + NF + R;
+            if (zb + NF <= -R || zb >= Nz + R || (zb >= 0 && zb + NF <= Nz)) continue;
+            const int nlo = M.nlo[l], nrows = M.nhi[l] - nlo;
+            if (nrows <= 0) continue;
+            const int ldlo = M.ldlo[l], ldhi = M.ldhi[l];
+            for (int fz = 0; fz < NF; ++fz) {
+                const int z = zb + fz;
+                if (!((z >= -R && z < 0) || (z >= Nz && z < Nz + R))) continue;
+                TF* slotb = ring + M.roff[l] + pmod(z, Q) * nrows * Xs;
+                for (int r = warp; r < nrows; r += NW)
+                    for (int c = ldlo + lane; c < ldhi; c += 32) stv<TF, V>(slotb + r * Xs + c * V, hvv);
+            }
+        }
+    };
+
+    const bool lock = P.CX > 1;
+    produce(s_begin);
+    cp_async_commit();
+    if (lock) cluster_arrive_relaxed();
+
+    for (int s = s_begin; s < s_end; ++s) {
+        produce(s + 1);
+        cp_async_commit();
+        // The stores below may overwrite (same parity array) values that another
+        // x-tile of this diamond loads in its overlap; those loads were issued at
+        // step s-2 or earlier and completed before that CTA's arrive of step s-1.
+        if (lock) cluster_wait();
 #pragma unroll
-                for (int r = 0; r < 2 * R; ++r) zr[r] = ldv<TF, V>(at(zfirst - R + r, y, col));
-                for (int z = zfirst; z < zlast; ++z) {
-                    zr[2 * R] = ldv<TF, V>(at(z + R, y, col));
+        for (int kk = 0; kk < K; ++kk) {
+            Item<TF, V>& I = it[kk];
+            if (!I.valid) continue;
+            const int zb = s * NF + I.zb0;
+            const int zfirst = zb < 0 ? 0 : zb;
+            const int zlast = zb + NF < Nz ? zb + NF : Nz;
+            if (zfirst >= zlast) continue;  // warp-uniform
+            int sl = pmod(zfirst - R, Q);   // slot of plane zfirst - R
+            if (!PERSIST || I.wz != zfirst) {
+#pragma unroll
+                for (int r = 0; r < 2 * R; ++r) {
+                    win[kk][r] = ldv<TF, V>(I.rowp + sl * I.PS);
+                    sl = wrap_inc(sl, Q);
+                }
+            } else {
+                sl += 2 * R;
+                if (sl >= Q) sl -= Q;
+            }
+            int sc = sl - R < 0 ? sl - R + Q : sl - R;  // slot of plane zfirst
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const int z = zfirst + f;
+                if (z < zlast) {
+                    win[kk][2 * R + f] = ldv<TF, V>(I.rowp + sl * I.PS);  // plane z + R
+                    const VT& ctr = win[kk][f + R];
+                    const TF* cp = I.rowp + sc * I.PS;
                     TF xl[(2 * J + 1) * V];
 #pragma unroll
-                    for (int q = -J; q <= J; ++q) {
-                        VT w = (q == 0) ? zr[R] : ldv<TF, V>(at(z, y, col + q * V));
+                    for (int e = 0; e < V; ++e) xl[J * V + e] = ctr.v[e];
 #pragma unroll
-                        for (int e = 0; e < V; ++e) xl[(q + J) * V + e] = w.v[e];
+                    for (int q = 1; q <= J; ++q) {
+                        VT lf{}, rt{};
+                        if (lane < q) lf = ldv<TF, V>(cp - q * V);
+                        if (lane >= 32 - q) rt = ldv<TF, V>(cp + (q <= I.qr ? q : I.qr) * V);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            if ((J - q) * V + e >= J * V - R) {  // within R to the left
+                                const TF w = __shfl_up_sync(0xffffffffu, ctr.v[e], q);
+                                xl[(J - q) * V + e] = lane < q ? lf.v[e] : w;
+                            }
+                            if ((J + q) * V + e <= J * V + V - 1 + R) {  // within R to the right
+                                const TF w = __shfl_down_sync(0xffffffffu, ctr.v[e], q);
+                                xl[(J + q) * V + e] = lane >= 32 - q ? rt.v[e] : w;
+                            }
+                        }
                     }
                     VT ypv[R], ymv[R];
 #pragma unroll
                     for (int r = 1; r <= R; ++r) {
-                        ypv[r - 1] = ldv<TF, V>(at(z, y + r, col));
-                        ymv[r - 1] = ldv<TF, V>(at(z, y - r, col));
+                        ypv[r - 1] = ldv<TF, V>(cp + r * Xs);
+                        ymv[r - 1] = ldv<TF, V>(cp - r * Xs);
                     }
-                    const size_t gidx = L.at(xg, y, z);
+                    const size_t gidx = I.g0 + (size_t)z * gplane;
                     Vec<TC, V> cv[NC > 0 ? NC : 1];
                     if constexpr (NC > 0) {
-                        if (xg < Nx) {
+                        if (I.active && I.indom) {
 #pragma unroll
                             for (int m = 0; m < NC; ++m) cv[m] = ldv_ro<TC, V>(P.C[m] + gidx);
                         } else {
@@ -317,16 +395,17 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
 #pragma unroll
                     for (int e = 0; e < V; ++e) {
                         const int xc = J * V + e;
-                        TF r_;
+                        const VT& zp1 = win[kk][f + R + 1];
+                        const VT& zm1 = win[kk][f + R - 1];
                         if constexpr (KIND == K7C) {
-                            r_ = upd7c<TF>(P.c0, P.c1, zr[R].v[e], xl[xc + 1], xl[xc - 1], ypv[0].v[e],
-                                           ymv[0].v[e], zr[R + 1].v[e], zr[R - 1].v[e]);
+                            out.v[e] = upd7c<TF>(P.c0, P.c1, ctr.v[e], xl[xc + 1], xl[xc - 1], ypv[0].v[e],
+                                                 ymv[0].v[e], zp1.v[e], zm1.v[e]);
                         } else if constexpr (KIND == K7V) {
                             TF c[7];
 #pragma unroll
                             for (int m = 0; m < 7; ++m) c[m] = Cvt<TF, TC>::f(cv[m].v[e]);
-                            r_ = upd7v<TF>(c, zr[R].v[e], xl[xc + 1], xl[xc - 1], ypv[0].v[e], ymv[0].v[e],
-                                           zr[R + 1].v[e], zr[R - 1].v[e]);
+                            out.v[e] = upd7v<TF>(c, ctr.v[e], xl[xc + 1], xl[xc - 1], ypv[0].v[e], ymv[0].v[e],
+                                                 zp1.v[e], zm1.v[e]);
                         } else {
                             TF c[13], xp[4], xm[4], yp4[4], ym4[4], zp[4], zm[4];
 #pragma unroll
@@ -337,44 +416,43 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
                                 xm[q] = xl[xc - q - 1];
                                 yp4[q] = ypv[q].v[e];
                                 ym4[q] = ymv[q].v[e];
-                                zp[q] = zr[R + q + 1].v[e];
-                                zm[q] = zr[R - q - 1].v[e];
+                                zp[q] = win[kk][f + R + q + 1].v[e];
+                                zm[q] = win[kk][f + R - q - 1].v[e];
                             }
-                            r_ = upd25v<TF>(c, zr[R].v[e], xp, xm, yp4, ym4, zp, zm);
-                        }
-                        out.v[e] = (xg + e < Nx) ? r_ : hv;
-                    }
-                    if (rdst) {
-                        TF* dp = rdst + ((size_t)pmod(z, Q) * dnrows + (y - dnlo)) * Xs;
-                        stv<TF, V>(dp + col, out);
-                        if (P.CX > 1) {
-                            if (xv < J && crank > 0) {
-                                TF* rp = cluster.map_shared_rank(dp + HV + Xt + xv * V, crank - 1);
-                                stv<TF, V>(rp, out);
-                            }
-                            if (xv >= G - J && crank < P.CX - 1) {
-                                TF* rp = cluster.map_shared_rank(dp + (xv - (G - J)) * V, crank + 1);
-                                stv<TF, V>(rp, out);
-                            }
+                            out.v[e] = upd25v<TF>(c, ctr.v[e], xp, xm, yp4, ym4, zp, zm);
                         }
                     }
-                    if (store && xg < Nx) {
-                        if (xg + V <= Nx) {
-                            stv<TF, V>(gdst + gidx, out);
+                    if (!I.full) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e)
+                            if (!(I.xg + e >= 0 && I.xg + e < Nx)) out.v[e] = hv;
+                    }
+                    if (I.active && I.dstp) stv<TF, V>(I.dstp + sc * I.dPS, out);
+                    if (I.store) {
+                        if (I.full) {
+                            stv<TF, V>(I.gdst + gidx, out);
                         } else {
 #pragma unroll
                             for (int e = 0; e < V; ++e)
-                                if (xg + e < Nx) gdst[gidx + e] = out.v[e];
+                                if (I.xg + e < Nx) I.gdst[gidx + e] = out.v[e];
                         }
                     }
-#pragma unroll
-                    for (int r = 0; r < 2 * R; ++r) zr[r] = zr[r + 1];
+                    sl = wrap_inc(sl, Q);
+                    sc = wrap_inc(sc, Q);
                 }
             }
+            if (PERSIST) {
+#pragma unroll
+                for (int r = 0; r < 2 * R; ++r) win[kk][r] = win[kk][r + NF];
+                I.wz = (zlast - zfirst == NF) ? zfirst + NF : -(1 << 30);
+            }
         }
-        cp_async_wait_all();
-        if (P.CX > 1) cluster.sync(); else __syncthreads();
+        cp_async_wait_1();
+        __syncthreads();
+        if (lock) cluster_arrive_relaxed();
     }
+    if (lock) cluster_wait();
+    cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------- host side
@@ -390,8 +468,10 @@ static int ring_rows_bound(int D, int R) {
     return rows;
 }
 
+static int item_bound(int D, int R) { return D * D / (2 * R); }
+
 struct BlkShape {
-    int V, HV, Xt, Xs, Q, G;
+    int V, HV, Xt, EH, Xs, Q, K;
     size_t smem;
     bool ok;
 };
@@ -404,16 +484,25 @@ static BlkShape blk_shape(const SweepArgs& a, const BlockedTune& tn) {
     int J = (R + s.V - 1) / s.V;
     s.HV = J * s.V;
     s.ok = false;
-    if (tn.dw < 2 * R || tn.dw % (2 * R) != 0 || tn.nf < 1 || tn.cx < 1 || tn.cx > 16) return s;
-    if (tn.dw / R - 1 > MAXLV) return s;
+    if (tn.dw < 2 * R || tn.dw % (2 * R) != 0) return s;
+    if (tn.nf < 1 || tn.nf > 2) return s;
+    int ltmax = tn.dw / R - 1;
+    if (ltmax > MAXLV) return s;
     if (tn.warps < 1 || tn.warps * 32 > BLK_MAXT) return s;
-    int per = (a.L.nx + tn.cx - 1) / tn.cx;
-    s.Xt = ((per + s.V - 1) / s.V) * s.V;
-    if (s.Xt < s.HV) s.Xt = s.HV;
-    s.G = s.Xt / s.V;
-    if (s.G > tn.warps * 32) return s;
-    s.Xs = s.Xt + 2 * s.HV;
-    s.Q = 2 * (tn.nf + R);
+    if (tn.xtile < s.V || tn.xtile % s.V != 0 || tn.xtile > 4096) return s;
+    if ((a.L.nx + tn.xtile - 1) / tn.xtile > MAXCLUSTER) return s;
+    // one warp of vectors covers a tile row plus its trapezoid overlap at every level
+    int ov = ltmax > 1 ? (R * (ltmax - 1) + s.V - 1) / s.V : 0;
+    if (tn.xtile / s.V + 2 * ov > 32) return s;
+    int items = item_bound(tn.dw, R);
+    if (items > MAXITEM) return s;
+    int K = (items + tn.warps - 1) / tn.warps;
+    if (K > 4) return s;
+    s.K = K <= 1 ? 1 : (K <= 2 ? 2 : 4);
+    s.Xt = tn.xtile;
+    s.EH = ((R * ltmax + s.V - 1) / s.V) * s.V + s.HV;
+    s.Xs = s.Xt + 2 * s.EH;
+    s.Q = 3 * tn.nf + 2 * R;
     s.smem = (size_t)s.Q * ring_rows_bound(tn.dw, R) * s.Xs * eb;
     s.ok = true;
     return s;
@@ -425,21 +514,15 @@ size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tn) {
     return s.smem + sizeof(TileMeta);
 }
 
-template <int KIND, typename TF, typename TC>
-static cudaError_t launch_blocked(const SweepArgs& a, void* const field[2], int p0, int T,
-                                  const BlockedTune& tn, cudaStream_t st) {
+template <int KIND, typename TF, typename TC, int K, int NF>
+static cudaError_t launch_blocked_k(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
+                                    const BlkShape& sh, cudaStream_t st, long long* launches) {
     const int R = KindTraits<KIND>::R;
-    BlkShape sh = blk_shape(a, tn);
-    if (!sh.ok) return cudaErrorInvalidValue;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (sh.smem + sizeof(TileMeta) > (size_t)optin) return cudaErrorInvalidValue;
-    auto kfn = blocked_kernel<KIND, TF, TC>;
+    auto kfn = blocked_kernel<KIND, TF, TC, K, NF>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
     if (e != cudaSuccess) return e;
-    if (tn.cx > 8) {
+    const int nxt = (a.L.nx + sh.Xt - 1) / sh.Xt;
+    if (nxt > 8) {
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
@@ -454,11 +537,11 @@ static cudaError_t launch_blocked(const SweepArgs& a, void* const field[2], int 
     P.p0 = p0;
     P.T = T;
     P.D = tn.dw;
-    P.NF = tn.nf;
     P.Xt = sh.Xt;
-    P.CX = tn.cx;
+    P.EH = sh.EH;
     P.Q = sh.Q;
     P.Xs = sh.Xs;
+    P.CX = nxt;
     const int D = tn.dw, Ny = a.L.ny;
     for (int k = 0;; ++k) {
         int tlo, thi;
@@ -484,42 +567,62 @@ static cudaError_t launch_blocked(const SweepArgs& a, void* const field[2], int 
         P.row = k;
         P.bmin = bmin;
         cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)tn.cx, (unsigned)(bmax - bmin + 1), 1);
+        cfg.gridDim = dim3((unsigned)nxt, (unsigned)(bmax - bmin + 1), 1);
         cfg.blockDim = dim3((unsigned)(tn.warps * 32), 1, 1);
         cfg.dynamicSmemBytes = sh.smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)tn.cx;
+        attr[0].val.clusterDim.x = (unsigned)nxt;
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
-        cfg.numAttrs = 1;
+        cfg.numAttrs = nxt > 1 ? 1 : 0;
         e = cudaLaunchKernelEx(&cfg, kfn, P);
         if (e != cudaSuccess) return e;
+        if (launches) ++*launches;
     }
     return cudaSuccess;
 }
 
+template <int KIND, typename TF, typename TC>
+static cudaError_t launch_blocked(const SweepArgs& a, void* const field[2], int p0, int T,
+                                  const BlockedTune& tn, cudaStream_t st, long long* launches) {
+    BlkShape sh = blk_shape(a, tn);
+    if (!sh.ok) return cudaErrorInvalidValue;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (sh.smem + sizeof(TileMeta) > (size_t)optin) return cudaErrorInvalidValue;
+#define STG_BLK(KK, NFF)                                                                                      \
+    if (sh.K == KK && tn.nf == NFF)                                                                           \
+        return launch_blocked_k<KIND, TF, TC, KK, NFF>(a, field, p0, T, tn, sh, st, launches);
+    STG_BLK(1, 1) STG_BLK(2, 1) STG_BLK(4, 1) STG_BLK(1, 2) STG_BLK(2, 2) STG_BLK(4, 2)
+#undef STG_BLK
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
-                        cudaStream_t s) {
+                        cudaStream_t s, long long* launches) {
     if (T <= 0 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
     switch (a.kind) {
         case K7C:
-            if (a.fdt == DT_F32) return launch_blocked<K7C, float, float>(a, field, p0, T, tn, s);
-            if (a.fdt == DT_F64) return launch_blocked<K7C, double, double>(a, field, p0, T, tn, s);
+            if (a.fdt == DT_F32) return launch_blocked<K7C, float, float>(a, field, p0, T, tn, s, launches);
+            if (a.fdt == DT_F64) return launch_blocked<K7C, double, double>(a, field, p0, T, tn, s, launches);
             break;
         case K7V:
-            if (a.fdt == DT_F32 && a.cdt == DT_F32) return launch_blocked<K7V, float, float>(a, field, p0, T, tn, s);
+            if (a.fdt == DT_F32 && a.cdt == DT_F32)
+                return launch_blocked<K7V, float, float>(a, field, p0, T, tn, s, launches);
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return launch_blocked<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, s);
-            if (a.fdt == DT_F64) return launch_blocked<K7V, double, double>(a, field, p0, T, tn, s);
+                return launch_blocked<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, s, launches);
+            if (a.fdt == DT_F64) return launch_blocked<K7V, double, double>(a, field, p0, T, tn, s, launches);
             break;
         case K25V:
-            if (a.fdt == DT_F32 && a.cdt == DT_F32) return launch_blocked<K25V, float, float>(a, field, p0, T, tn, s);
+            if (a.fdt == DT_F32 && a.cdt == DT_F32)
+                return launch_blocked<K25V, float, float>(a, field, p0, T, tn, s, launches);
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return launch_blocked<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, s);
-            if (a.fdt == DT_F64) return launch_blocked<K25V, double, double>(a, field, p0, T, tn, s);
+                return launch_blocked<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, s, launches);
+            if (a.fdt == DT_F64) return launch_blocked<K25V, double, double>(a, field, p0, T, tn, s, launches);
             break;
     }
     return cudaErrorInvalidValue;

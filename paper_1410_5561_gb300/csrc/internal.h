@@ -24,12 +24,12 @@ struct SweepArgs {
     double halo;           // Dirichlet value of every halo cell
 };
 
-// Blocked-sweep tunables (D_w, N_F, warps per CTA, CTAs per cluster along x).
+// Blocked-sweep tunables (D_w, N_F, warps per CTA, x-tile width).
 struct BlockedTune {
     int dw;       // diamond width in y (multiple of 2R)
     int nf;       // frontlines: z-planes per level per wavefront step
     int warps;    // warps per CTA
-    int cx;       // CTAs per cluster, splitting x
+    int xtile;    // x columns owned by one CTA (multiple of the vector width)
 };
 
 // One plain step: dst(interior) = A src.
@@ -41,7 +41,7 @@ cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s);
 // Temporally blocked run of T steps from parity p0 (array (p0 + t) & 1 holds u_t).
 // Returns cudaErrorInvalidValue for an infeasible tuning, after checking it on the host.
 cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T,
-                        const BlockedTune& tune, cudaStream_t s);
+                        const BlockedTune& tune, cudaStream_t s, long long* launches);
 
 // Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);

@@ -27,19 +27,30 @@ def kind_id(kind) -> int:
 
 @dataclass
 class Tuning:
-    """Blocked-schedule tunables: diamond width D_w, frontlines N_F, warps per CTA,
-    CTAs per cluster along x (Section II-A's thread group)."""
+    """Blocked-schedule tunables: diamond width D_w, frontlines N_F, warps per CTA
+    (the thread group sharing one extruded diamond), x columns per CTA."""
     dw: int
     nf: int = 1
     warps: int = 8
-    xsplit: int = 1
+    xtile: int = 128
 
     def c(self) -> C.stencil_tuning:
-        return C.stencil_tuning(self.dw, self.nf, self.warps, self.xsplit)
+        return C.stencil_tuning(self.dw, self.nf, self.warps, self.xtile)
 
 
 def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
+
+
+def probe_fma_peak(dtype=torch.float32, iters: int = 4096, device=None) -> float:
+    """Measured vector FMA throughput in flop/s (two flops per FMA) on the current device."""
+    scratch = torch.empty(65536, dtype=torch.uint8, device=device or "cuda")
+    stream = torch.cuda.current_stream(scratch.device)
+    sec = ctypes.c_double(0.0)
+    fl = ctypes.c_double(0.0)
+    C.call("stencil_probe_fma", DTYPES[dtype], int(iters), _ptr(scratch),
+           ctypes.c_void_p(stream.cuda_stream), ctypes.byref(sec), ctypes.byref(fl))
+    return fl.value / sec.value
 
 
 class Stencil:
@@ -144,6 +155,13 @@ class Stencil:
 
     def run(self, T: int):
         C.call("stencil_run", self._h, int(T))
+
+    @property
+    def launches(self) -> int:
+        """Kernels this grid has launched so far."""
+        n = ctypes.c_longlong(0)
+        C.call("stencil_launch_count", self._h, ctypes.byref(n))
+        return int(n.value)
 
     def sync(self):
         C.call("stencil_sync", self._h)

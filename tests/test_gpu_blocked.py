@@ -23,12 +23,13 @@ def _run(p, T, scheme, tuning=None):
     return s.get_field().cpu().numpy()
 
 
-R1_TUNINGS = [Tuning(4, 1, 4, 1), Tuning(8, 1, 8, 2), Tuning(8, 2, 8, 3), Tuning(16, 1, 16, 4),
-              Tuning(12, 3, 4, 1), Tuning(2, 1, 2, 1), Tuning(24, 1, 8, 2)]
-R4_TUNINGS = [Tuning(8, 1, 8, 1), Tuning(16, 1, 8, 2), Tuning(16, 2, 16, 3), Tuning(32, 1, 8, 4)]
+# Tuning(D_w, N_F, warps, xtile); small x tiles force several x-tiles per diamond
+R1_TUNINGS = [Tuning(4, 1, 4, 16), Tuning(8, 1, 8, 8), Tuning(8, 2, 8, 12), Tuning(10, 1, 16, 8),
+              Tuning(6, 2, 8, 20), Tuning(2, 1, 2, 4), Tuning(10, 2, 16, 16)]
+R4_TUNINGS = [Tuning(8, 1, 8, 8), Tuning(16, 1, 8, 12), Tuning(8, 2, 8, 16), Tuning(8, 2, 4, 20)]
 
 
-@pytest.mark.parametrize("tn", R1_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xsplit}")
+@pytest.mark.parametrize("tn", R1_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xtile}")
 @pytest.mark.parametrize("kind,shape,fdt,cdt", [
     ("7pt_const", (45, 37, 23), "f32", None),
     ("7pt_var", (33, 29, 19), "f32", None),
@@ -43,7 +44,7 @@ def test_blocked_bitwise_equals_plain_r1(kind, shape, fdt, cdt, tn, T):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("tn", R4_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xsplit}")
+@pytest.mark.parametrize("tn", R4_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xtile}")
 @pytest.mark.parametrize("shape,fdt", [((29, 35, 21), "f32"), ((18, 25, 14), "f64")])
 @pytest.mark.parametrize("T", [1, 5, 9])
 def test_blocked_bitwise_equals_plain_r4(shape, fdt, tn, T):
@@ -54,10 +55,10 @@ def test_blocked_bitwise_equals_plain_r4(shape, fdt, tn, T):
 
 
 @pytest.mark.parametrize("kind,shape,fdt,T,tn", [
-    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(8, 1, 8, 1)),
-    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(16, 2, 8, 2)),
-    ("7pt_var", (50, 47, 31), "f32", 10, Tuning(8, 1, 8, 2)),
-    ("25pt_var", (40, 33, 30), "f32", 6, Tuning(16, 1, 8, 2)),
+    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(8, 1, 8, 48)),
+    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(10, 1, 16, 16)),
+    ("7pt_var", (50, 47, 31), "f32", 10, Tuning(8, 1, 8, 16)),
+    ("25pt_var", (40, 33, 30), "f32", 6, Tuning(16, 1, 8, 20)),
 ])
 def test_blocked_matches_oracle(kind, shape, fdt, T, tn):
     p = Problem(kind, *shape, fdt=fdt, seed=13)
@@ -70,7 +71,7 @@ def test_blocked_matches_oracle(kind, shape, fdt, T, tn):
 def test_blocked_small_and_degenerate_shapes():
     for shape in [(1, 1, 1), (5, 2, 3), (9, 3, 40), (64, 1, 5), (3, 70, 2)]:
         p = Problem("7pt_var", *shape, fdt="f32", seed=14, halo=0.5)
-        for tn in [Tuning(4, 1, 4, 1), Tuning(8, 2, 8, 2)]:
+        for tn in [Tuning(4, 1, 4, 4), Tuning(8, 2, 8, 16)]:
             a = _run(p, 7, "plain")
             b = _run(p, 7, "blocked", tn)
             assert np.array_equal(a, b), (shape, tn)
@@ -79,7 +80,7 @@ def test_blocked_small_and_degenerate_shapes():
 def test_blocked_successive_runs_and_parity():
     p = Problem("7pt_const", 40, 40, 40, fdt="f32", seed=15)
     s = p.make()
-    s.set_tuning("blocked", Tuning(8, 1, 8, 2))
+    s.set_tuning("blocked", Tuning(8, 1, 8, 16))
     s.run(3)
     s.run(4)
     s.run(0)
@@ -97,6 +98,14 @@ def test_infeasible_tuning_rejected():
     with pytest.raises(StencilError):
         s.set_tuning("blocked", Tuning(7, 1, 8, 1))    # D_w not a multiple of 2R
     with pytest.raises(StencilError):
-        s.set_tuning("blocked", Tuning(64, 8, 8, 1))   # rings far beyond shared memory
+        s.set_tuning("blocked", Tuning(64, 8, 8, 64))  # rings far beyond shared memory
     with pytest.raises(StencilError):
-        s.set_tuning("blocked", Tuning(8, 1, 8, 17))   # cluster too large
+        s.set_tuning("blocked", Tuning(8, 1, 8, 6))    # x tile not a multiple of 4 floats
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(8, 1, 8, 128))  # tile row plus overlap wider than a warp
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(8, 3, 8, 64))   # more than two frontlines
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(16, 1, 16, 64))  # 128 rows exceed 16 warps x 4 rows
+    with pytest.raises(StencilError):
+        s.set_tuning("blocked", Tuning(8, 1, 8, 2))    # x tile narrower than one vector

@@ -1,0 +1,493 @@
+#!/usr/bin/env python3
+"""GLUP/s and HBM bytes per LUP of the temporally blocked vs the plain sweep on GB300.
+
+One step = one stencil_run(T = 100) of the 7-point constant-coefficient Jacobi
+sweep (Listing 1, c0 = 0.4, c1 = 0.1) on a 1024^3 FP32 interior with a zero
+Dirichlet halo, through the temporally blocked schedule with an autotuned
+tuning; the plain one-step sweep is timed beside it, and (on one GPU) every
+other stencil of the library is measured plain vs blocked as well.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own replica (the sweep does not
+shard across GPUs here: replicas only); the reported value is the aggregate
+GLUP/s over the max-over-ranks time. `--impl reference` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLUP/s and ncu HBM bytes/LUP, blocked vs plain sweep on one GB300, per stencil"
+HEADLINE = dict(kind="7pt_const", n=1024, fdt="f32", cdt=None, T=100)
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "blocked_kernel_7pt_const_f32_traffic.txt")
+CPU_SAMPLE_N = 256
+CPU_BASELINE_N = 512
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-stencil table")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--case", default=None,
+                    help="profiling helper: KIND:N:FIELD:COEF:SCHEME:T[:dw,nf,warps,xtile] runs that "
+                         "case twice and exits (no JSON)")
+    return ap.parse_args()
+
+
+def run_case(spec: str, seed: int):
+    """Set up one grid and run it twice (used for ncu captures of single kernels)."""
+    import torch
+    from paper_1410_5561_gb300.stencil import Tuning
+    parts = spec.split(":")
+    kind, n, fdt, cdt, scheme, T = parts[0], int(parts[1]), parts[2], parts[3], parts[4], int(parts[5])
+    tn = Tuning(*[int(v) for v in parts[6].split(",")]) if len(parts) > 6 else None
+    s, _ = make_grid(kind, n, fdt, None if cdt in ("", "-") else cdt, seed, torch.device("cuda", 0))
+    s.set_tuning(scheme, tn)
+    for _ in range(2):
+        s.run(T)
+        s.sync()
+    print("case done", spec, flush=True)
+    return 0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- CPU oracle arm
+
+def cpu_oracle_sample(budget_s: float = 15.0, n: int = CPU_BASELINE_N, seed: int = 0):
+    """Time the FP64 oracle (7-point constant, Listing 1) on an n^3 sample on the host
+    cores; T is chosen so the sample takes about ``budget_s`` seconds."""
+    import oracle
+    from paper_1410_5561_gb300 import inputs
+    u0 = inputs.field_u0(seed, n, n, n)
+    t0 = time.perf_counter()
+    oracle.sweep("7pt_const", u0, 1)
+    t1 = max(time.perf_counter() - t0, 1e-4)
+    T = max(1, min(1000, int(budget_s / t1)))
+    t0 = time.perf_counter()
+    oracle.sweep("7pt_const", u0, T)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": n ** 3 * T / dt / 1e9, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+            "sample": f"7pt-const FP64 oracle, {n}^3 interior, T={T} steps ({dt:.1f} s), OpenMP over k"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1410_5561_gb300 import inputs
+    n = CPU_SAMPLE_N
+    u0 = inputs.field_u0(args.seed, n, n, n)
+    t0 = time.perf_counter()
+    oracle.sweep("7pt_const", u0, 1)
+    t1 = max(time.perf_counter() - t0, 1e-4)
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    T = max(1, min(200, int(budget / t1)))
+    for _ in range(args.warmup):
+        oracle.sweep("7pt_const", u0, T)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sweep("7pt_const", u0, T)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = n ** 3 * T * len(times) / tot / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    sample = f"7pt-const FP64 oracle, {n}^3 interior, T={T} steps per step, OpenMP over k"
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "7-point constant-coefficient Jacobi sweep (Listing 1), FP64 CPU oracle, "
+                               f"bounded sample {n}^3 x T={T} of the 1024^3 T=100 workload",
+                   "stencil": "7pt_const", "grid": [n, n, n], "T": T},
+        "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- GPU helpers
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx), "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def make_grid(kind, n, fdt, cdt, seed, device):
+    """A Stencil with seeded inputs generated on the device (same values as the CPU recipe's
+    draws; coefficients normalised as in paper_1410_5561_gb300.inputs)."""
+    import torch
+    from paper_1410_5561_gb300 import inputs
+    from paper_1410_5561_gb300.stencil import Stencil
+    tdt = {"f32": torch.float32, "f64": torch.float64}[fdt]
+    tcd = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[cdt or fdt]
+    s = Stencil(kind, n, n, n, dtype=tdt, coef_dtype=tcd, device=device)
+    u0 = torch.empty((n, n, n), dtype=tdt, device=device)
+    inputs.fill_uniform_torch(u0, seed, inputs.STREAM_U0, -1.0, 1.0)
+    if kind == "7pt_const":
+        s.set_coeffs(scalars=(0.4, 0.1))
+    else:
+        nc = 7 if kind == "7pt_var" else 13
+        acc = None
+        rs = []
+        for m in range(nc):
+            r = torch.empty((n, n, n), dtype=torch.float64, device=device)
+            inputs.fill_uniform_torch(r, seed, inputs.STREAM_COEF0 + m, 0.0, 1.0)
+            w = r if (kind == "7pt_var" or m == 0) else 2.0 * r
+            acc = w.clone() if acc is None else acc.add_(w)
+            rs.append(r)
+        for m in range(nc):
+            rs[m] = (0.95 * rs[m] / acc).to(tcd)
+        del acc
+        s.set_coeffs(arrays=rs)
+        del rs
+    s.set_field(u0, halo=0.0)
+    torch.cuda.synchronize(device)
+    return s, u0
+
+
+def timed(s, T, steps, warmup, barrier=None):
+    """Seconds for ``steps`` runs of T steps, CUDA events on the grid's stream."""
+    import torch
+    for _ in range(warmup):
+        s.run(T)
+    torch.cuda.synchronize(s.device)
+    if barrier:
+        barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    for _ in range(steps):
+        s.run(T)
+    e1.record(s.stream)
+    e1.synchronize()
+    torch.cuda.synchronize(s.device)
+    if barrier:
+        barrier()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def traffic_from_profile(kernel_src_hash: str):
+    """dram bytes per LUP recorded by the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    vals = {}
+    with open(PROFILE_TRAFFIC) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256") != kernel_src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_lup"]), vals
+    except (KeyError, ValueError):
+        return None
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for name in ("blocked.cu", "common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1410_5561_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def run_ours(args):
+    import torch
+    from paper_1410_5561_gb300 import model, tuner
+    from paper_1410_5561_gb300.stencil import probe_fma_peak
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier(device_ids=[device.index])
+
+    def maxall(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    hbm_peak, peak_src = peaks()
+    fp32_peak = probe_fma_peak(torch.float32, device=device)
+    fp64_peak = probe_fma_peak(torch.float64, iters=512, device=device)
+
+    H = HEADLINE
+    n, T = H["n"], H["T"]
+    s, u0 = make_grid(H["kind"], n, H["fdt"], H["cdt"], args.seed, device)
+    lups = float(n) ** 3 * T
+
+    # autotune the blocked schedule on the real grid, then reset the field
+    tn, table = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+    s.set_field(u0, halo=0.0)
+
+    # headline: blocked
+    for _ in range(args.warmup):
+        s.run(T)
+    clocks = ClockSampler(device.index)
+    l0 = s.launches
+    clocks.start()
+    t_blk = timed(s, T, args.steps, 0, barrier)
+    clk = clocks.stop()
+    launches_timed = s.launches - l0
+    t_blk = maxall(t_blk)
+    value = world * lups * args.steps / t_blk / 1e9
+
+    # plain beside it
+    s.set_tuning("plain")
+    ksteps = max(1, min(2, args.steps))
+    t_plain = maxall(timed(s, T, ksteps, 1, barrier))
+    plain_glups = lups * ksteps / t_plain / 1e9
+    s.set_tuning("blocked", tn)
+
+    # sampled error vs the FP64 oracle (rank 0, one GPU)
+    err = None
+    if rank == 0 and world == 1:
+        import numpy as np
+        import oracle
+        s.set_field(u0, halo=0.0)
+        s.run(T)
+        got = s.current
+        pts = [(1, 2, 3), (n // 2, n // 3, n // 5), (n - 1, n - 2, n // 2), (n // 7, n - 1, n - 3)]
+        sc = (float(np.float32(0.4)), float(np.float32(0.1)))
+        ref, g = [], []
+        for (i, j, k) in pts:
+            # the point depends on u0 within R*T cells; a crop with one more cell of margin,
+            # clipped to the grid, keeps every value it depends on (the crop's own edges
+            # are farther than R*T away unless they are the grid's Dirichlet faces)
+            m = T + 1
+            lo = [max(0, c - m) for c in (k, j, i)]
+            hi = [min(n, c + m + 1) for c in (k, j, i)]
+            crop = u0[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]].double().cpu().numpy()
+            ref.append(oracle.points("7pt_const", crop, T, [(i - lo[2], j - lo[1], k - lo[0])], scalars=sc)[0])
+            g.append(float(got[k, j, i]))
+        ref, g = np.array(ref), np.array(g)
+        err = float(np.max(np.abs(g - ref)) / max(np.max(np.abs(ref)), 1e-30))
+
+    # end to end through the public API: host (pinned) in, host out, copies timed
+    e2e = None
+    if world >= 1:
+        host_in = u0.cpu().pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        s.set_field(host_in, halo=0.0)
+        s.run(T)
+        s.get_field(host_out)
+        barrier()
+        ke = max(1, min(2, args.steps))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            s.set_field(host_in, halo=0.0)
+            s.run(T)
+            s.get_field(host_out)
+        te = maxall(time.perf_counter() - t0)
+        nbytes = host_in.numel() * host_in.element_size()
+        e2e = {"value": world * lups * ke / te / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes}
+        del host_in, host_out
+
+    # roofline of the blocked kernel (algorithmic bytes per LUP: Eq. 5 with FP32 sizes)
+    bpl = model.bytes_per_lup("7pt_const", "f32", None, "blocked", tn.dw)
+    achieved_gbs = bpl * lups * args.steps / t_blk / 1e9  # per GPU
+    fp_time = model.FP_INSTR["7pt_const"] * 2 / fp32_peak
+    hbm_time = bpl / (hbm_peak * 1e9)
+    bound = "hbm" if hbm_time >= fp_time else "alu"
+    prof = traffic_from_profile(src_hash())
+    launches_per_step = max(1, launches_timed // max(1, args.steps))
+    traffic = None
+    if prof is not None:
+        traffic = prof[0] * lups / launches_per_step
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_lup": bpl}
+    else:
+        ach = model.FLOPS["7pt_const"] * lups * args.steps / t_blk / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach / (fp32_peak / 1e12), "traffic": traffic}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_blk / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"7-point constant-coefficient Jacobi sweep (Listing 1, c0=0.4, c1=0.1), "
+                               f"{n}^3 interior FP32, zero Dirichlet halo, T={T} per step, temporally blocked "
+                               f"(D_w={tn.dw}, N_F={tn.nf}, warps={tn.warps}, xtile={tn.xtile})",
+                   "stencil": "7pt_const", "grid": [n, n, n], "T": T, "scheme": "blocked",
+                   "tuning": {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile},
+                   "l2": f"inputs larger than L2 ({(n + 2) ** 3 * 4 / 1e9:.1f} GB per array)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "plain": {"value": plain_glups * world, "unit": "GLUP/s", "ms_per_step": 1e3 * t_plain / ksteps,
+                  "algorithmic_bytes_per_lup": model.bytes_per_lup("7pt_const", "f32", None, "plain")},
+        "blocked_over_plain": value / (plain_glups * world),
+        "roofline": roof,
+        "gpu_launches": int(launches_timed),
+        "clocks": clk,
+        "e2e": e2e,
+        "err_vs_oracle_sampled": err,
+        "fma_peaks_tflops": {"f32": fp32_peak / 1e12, "f64": fp64_peak / 1e12},
+        "autotune": [{"tuning": f"dw={t.dw} nf={t.nf} warps={t.warps} xtile={t.xtile}", "s": sec}
+                     for t, sec in table],
+    }
+    del s, u0
+    torch.cuda.empty_cache()
+
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_oracle_sample()
+        if not args.no_extras:
+            try:
+                line["per_stencil"] = per_stencil(device, args.seed, hbm_peak, fp32_peak, fp64_peak)
+            except Exception as exc:  # report, never hide the headline
+                line["per_stencil_error"] = repr(exc)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier(device_ids=[device.index])
+        dist.destroy_process_group()
+    return 0
+
+
+PER_STENCIL = [
+    ("7pt_const", 512, "f32", None, 100),
+    ("7pt_const", 512, "f64", None, 100),
+    ("7pt_var", 384, "f32", None, 50),
+    ("7pt_var", 384, "f32", "bf16", 50),
+    ("7pt_var", 384, "f64", None, 50),
+    ("25pt_var", 256, "f32", None, 40),
+]
+
+
+def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
+    import torch
+    from paper_1410_5561_gb300 import model, tuner
+    rows = []
+    for kind, n, fdt, cdt, T in PER_STENCIL:
+        s, u0 = make_grid(kind, n, fdt, cdt, seed, device)
+        lups = float(n) ** 3 * T
+        s.set_tuning("plain")
+        tp = timed(s, T, 2, 1) / 2
+        try:
+            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+            tb = timed(s, T, 2, 1) / 2
+            tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
+            bb = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)
+        except RuntimeError:
+            tb, tun, bb = None, None, None
+        bp = model.bytes_per_lup(kind, fdt, cdt, "plain")
+        peak_fp = fp64_peak if fdt == "f64" else fp32_peak
+        alu_t = model.FP_INSTR[kind] * 2 / peak_fp
+        rows.append({
+            "stencil": kind, "grid": n, "field": fdt, "coef": cdt or fdt, "T": T,
+            "plain_glups": lups / tp / 1e9,
+            "blocked_glups": lups / tb / 1e9 if tb else None,
+            "blocked_tuning": tun,
+            "model_bytes_per_lup": {"plain": bp, "blocked": bb},
+            "roofline_glups": {"hbm_plain": hbm_peak / bp, "hbm_blocked": hbm_peak / bb if bb else None,
+                               "alu": 1e-9 / alu_t},
+        })
+        del s, u0
+        torch.cuda.empty_cache()
+    return rows
+
+
+def main():
+    args = parse()
+    if args.case:
+        return run_case(args.case, args.seed)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -83,6 +83,39 @@ def fill_uniform(out: np.ndarray, seed: int, stream: int, lo: float, hi: float) 
     return out
 
 
+def _mix_torch(z):
+    """SplitMix64 mix on int64 tensors (two's-complement wrap; logical shifts by masking)."""
+    import torch
+    def shr(x, k):
+        return (x >> k) & ((1 << (64 - k)) - 1)
+    z = z ^ shr(z, 30)
+    z = z * _s64(0xBF58476D1CE4E5B9)
+    z = z ^ shr(z, 27)
+    z = z * _s64(0x94D049BB133111EB)
+    z = z ^ shr(z, 31)
+    return z
+
+
+def _s64(u: int) -> int:
+    u &= 0xFFFFFFFFFFFFFFFF
+    return u - (1 << 64) if u >= (1 << 63) else u
+
+
+def fill_uniform_torch(out, seed: int, stream: int, lo: float, hi: float, chunk: int = 1 << 24):
+    """Same values as :func:`fill_uniform`, computed with torch ops on ``out``'s device."""
+    import torch
+    flat = out.view(-1)
+    key = _s64(int(stream_key(seed, stream)))
+    g = _s64(0x9E3779B97F4A7C15)
+    for s0 in range(0, flat.numel(), chunk):
+        c = min(chunk, flat.numel() - s0)
+        n = torch.arange(s0 + 1, s0 + c + 1, dtype=torch.int64, device=out.device)
+        x = _mix_torch(n * g + key)
+        u = ((x >> 11) & ((1 << 53) - 1)).to(torch.float64) * (2.0 ** -53)
+        flat[s0:s0 + c] = (lo + (hi - lo) * u).to(out.dtype)
+    return out
+
+
 def uniform(seed: int, stream: int, shape, lo: float = 0.0, hi: float = 1.0,
             dtype=np.float64) -> np.ndarray:
     out = np.empty(tuple(shape), dtype=dtype)

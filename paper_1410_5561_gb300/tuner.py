@@ -1,0 +1,127 @@
+"""Autotuner for the blocked schedule.
+
+Section II-A: the diamond width and the number of frontlines are chosen by
+auto-tuning, with the search space pruned to blocks that fit the cache and
+that give enough concurrency. Here the "cache" is one CTA's shared memory (the
+library reports the exact ring footprint of a tuning, and tunings that do not
+fit the opt-in limit are dropped), candidates are ranked by the Eq. 5 code
+balance (smaller first, Section III-C) and each survivor is timed on the device
+with CUDA events. Results are cached per (stencil, dtypes, shape, T).
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import model
+from .stencil import NCOEF, RADIUS, Stencil, Tuning
+
+_CACHE: dict = {}
+_KIND_NAME = {0: "7pt_const", 1: "7pt_var", 2: "25pt_var"}
+_DT_NAME = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16"}
+
+
+def one_warp_xtile(dw: int, r: int, v: int) -> int:
+    """Widest x tile whose bottom-level row (tile plus trapezoid overlap) fits 32 vectors."""
+    lt = dw // r - 1
+    ov = math.ceil(r * (lt - 1) / v) if lt > 1 else 0
+    return max(v, (32 - 2 * ov) * v)
+
+
+def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tuning]:
+    """Tunings that fit shared memory, best model code balance first."""
+    r = RADIUS[s.kind]
+    eb = torch.empty((), dtype=s.dtype).element_size()
+    v = 16 // eb
+    optin = torch.cuda.get_device_properties(s.device).shared_memory_per_block_optin
+    max_dw = max_dw or 16 * r
+    out = []
+    for dw in range(2 * r, max_dw + 1, 2 * r):
+        xt = one_warp_xtile(dw, r, v)
+        for xtile in sorted({xt, max(v, (xt // 2) // v * v)}, reverse=True):
+            for nf in nfs:
+                for w in warps:
+                    t = Tuning(dw, nf, w, xtile)
+                    need = s.blocked_smem_bytes(t)
+                    if 0 < need <= optin:
+                        out.append(t)
+    kind = _KIND_NAME[s.kind]
+    fdt = _DT_NAME[s.dtype]
+    cdt = _DT_NAME[s.coef_dtype]
+    out.sort(key=lambda t: (model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw), -t.nf, -t.warps))
+    return out
+
+
+def _time_run(s: Stencil, T: int, reps: int) -> float:
+    s.run(T)
+    torch.cuda.synchronize(s.device)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        e0.record(s.stream)
+        s.run(T)
+        e1.record(s.stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return best
+
+
+def autotune(s: Stencil, T: int, reps: int = 2, max_candidates: int = 10, include_plain: bool = True,
+             use_cache: bool = True):
+    """Pick the fastest schedule for ``T`` steps of grid ``s``.
+
+    Returns (scheme, tuning or None, table) where table lists (label, seconds).
+    The grid's field advances while timing; callers reset it afterwards.
+    """
+    key = (s.kind, s.dtype, s.coef_dtype, s.nx, s.ny, s.nz, T)
+    if use_cache and key in _CACHE:
+        scheme, tn, table = _CACHE[key]
+        s.set_tuning(scheme, tn)
+        return scheme, tn, table
+    table = []
+    best = (float("inf"), "plain", None)
+    if include_plain:
+        s.set_tuning("plain")
+        t = _time_run(s, T, reps)
+        table.append(("plain", t))
+        best = (t, "plain", None)
+    for tn in candidates(s)[:max_candidates]:
+        try:
+            s.set_tuning("blocked", tn)
+        except Exception:
+            continue
+        t = _time_run(s, T, reps)
+        table.append((f"blocked dw={tn.dw} nf={tn.nf} warps={tn.warps} xtile={tn.xtile}", t))
+        if t < best[0]:
+            best = (t, "blocked", tn)
+    _, scheme, tn = best
+    s.set_tuning(scheme, tn)
+    _CACHE[key] = (scheme, tn, table)
+    return scheme, tn, table
+
+
+def best_blocked(s: Stencil, T: int, reps: int = 2, max_candidates: int = 10):
+    """The fastest blocked tuning only (for reporting blocked against plain)."""
+    key = ("blocked",) + (s.kind, s.dtype, s.coef_dtype, s.nx, s.ny, s.nz, T)
+    if key in _CACHE:
+        tn, table = _CACHE[key]
+        s.set_tuning("blocked", tn)
+        return tn, table
+    table = []
+    best = (float("inf"), None)
+    for tn in candidates(s)[:max_candidates]:
+        try:
+            s.set_tuning("blocked", tn)
+        except Exception:
+            continue
+        t = _time_run(s, T, reps)
+        table.append((tn, t))
+        if t < best[0]:
+            best = (t, tn)
+    if best[1] is None:
+        raise RuntimeError("no feasible blocked tuning")
+    s.set_tuning("blocked", best[1])
+    _CACHE[key] = (best[1], table)
+    return best[1], table

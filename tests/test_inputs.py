@@ -65,3 +65,16 @@ def test_bf16_rounding_is_nearest_even():
     assert r[2] == 1.0 + 2 ** -7          # above the tie -> up
     assert r[3] == 1.0 + 4 * 2 ** -8      # tie -> even (up)
     assert abs(r[4] + 0.95) < 2 ** -8
+
+
+def test_torch_generator_matches_numpy():
+    torch = __import__("pytest").importorskip("torch")
+    a = torch.empty(3, 7, 11, dtype=torch.float64)
+    inputs.fill_uniform_torch(a, 5, 2, -1.0, 1.0, chunk=37)
+    b = inputs.uniform(5, 2, (3, 7, 11), -1.0, 1.0)
+    assert np.array_equal(a.numpy(), b)
+    f = torch.empty(5, 5, 5, dtype=torch.float32)
+    inputs.fill_uniform_torch(f, 0, 0, -1.0, 1.0)
+    g = np.empty((5, 5, 5), dtype=np.float32)
+    inputs.fill_uniform(g, 0, 0, -1.0, 1.0)
+    assert np.array_equal(f.numpy(), g)

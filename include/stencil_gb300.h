@@ -51,7 +51,7 @@ enum stencil_kind { STENCIL_7PT_CONST = 0, STENCIL_7PT_VAR = 1, STENCIL_25PT_VAR
 enum stencil_dtype { STENCIL_F32 = 0, STENCIL_F64 = 1, STENCIL_BF16 = 2 };
 enum stencil_scheme { STENCIL_PLAIN = 0, STENCIL_BLOCKED = 1, STENCIL_AUTO = 2 };
 enum stencil_where { STENCIL_HOST = 0, STENCIL_DEVICE = 1 };
-enum stencil_array { STENCIL_FIELD_ARRAY = 0, STENCIL_COEF_ARRAY = 1 };
+enum stencil_array { STENCIL_FIELD_ARRAY = 0, STENCIL_COEF_ARRAY = 1, STENCIL_GRAD_ARRAY = 2 };
 
 enum stencil_status {
     STENCIL_OK = 0,
@@ -94,8 +94,9 @@ typedef struct {
 int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_dtype, int coef_dtype,
                    void* cuda_stream);
 
-/* Layout of the field (which = STENCIL_FIELD_ARRAY) or of one coefficient
- * array (STENCIL_COEF_ARRAY) of this grid. */
+/* Layout of the field (which = STENCIL_FIELD_ARRAY), of one coefficient array
+ * (STENCIL_COEF_ARRAY) or of one FP64 coefficient-gradient array
+ * (STENCIL_GRAD_ARRAY, same element index, 8-byte elements) of this grid. */
 int stencil_layout_of(stencil_t h, int which, stencil_layout* out);
 
 /* Bytes of device workspace run() needs (caller-allocated, passed to bind;
@@ -136,6 +137,34 @@ int stencil_parity(stencil_t h);
 /* Copy the current field's interior to dense dst (host or device). With
  * where = STENCIL_HOST the call waits for the stream. */
 int stencil_get_field(stencil_t h, void* dst, int where);
+
+/* ---- Adjoint (reverse mode) of the variable-coefficient sweeps (Listings 2, 3).
+ * For a cotangent lambda_T of u_T (for L = 0.5 ||u_T - target||^2 it is
+ * u_T - target): lambda_t = A^T lambda_{t+1}, dL/du_0 = lambda_0 and
+ * dL/dC_m(p) = sum_t lambda_{t+1}(p) x (the field value multiplying C_m(p) in
+ * step t). States are kept at every k-th step (k = ckpt_every, or ceil(sqrt(T))
+ * when ckpt_every <= 0) and the steps in between are recomputed during the
+ * backward pass. The coefficient gradients accumulate in FP64. */
+
+/* Workspace bytes both calls below need for (T, ckpt_every): (ceil(T/k) + k + 2)
+ * field arrays. */
+size_t stencil_adjoint_workspace_bytes(stencil_t h, int T, int ckpt_every);
+
+/* Like stencil_run(h, T), and stores the checkpoints u_0, u_k, u_2k, ... in
+ * workspace (device, stencil_adjoint_workspace_bytes long). Uses the schedule
+ * chosen by stencil_set_tuning for the forward steps. STENCIL_ENOTSUP for the
+ * 7-point constant-coefficient stencil. */
+int stencil_run_checkpointed(stencil_t h, int T, int ckpt_every, void* workspace, size_t workspace_bytes);
+
+/* Backward pass after stencil_run_checkpointed(h, T, ckpt_every, workspace, ...)
+ * with the same coefficients. lambda_T: device, field layout, the cotangent of
+ * u_T on the interior (its halo is ignored). g_u0: device, field layout; gets
+ * dL/du_0 on the interior and 0 elsewhere. g_coef[m], m < n_c: device, gradient
+ * layout (STENCIL_GRAD_ARRAY, FP64); overwritten with dL/dC_m on the interior and
+ * 0 elsewhere. Asynchronous on the handle's stream; the workspace's checkpoints
+ * are read, its other buffers overwritten. */
+int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T, void* g_u0, void* const* g_coef,
+                        void* workspace, size_t workspace_bytes);
 
 /* Shared-memory bytes per CTA the blocked kernel needs for a tuning (0 if the
  * tuning is malformed); the device limit is cudaDevAttrMaxSharedMemoryPerBlockOptin. */

@@ -16,7 +16,7 @@ STENCIL_7PT_CONST, STENCIL_7PT_VAR, STENCIL_25PT_VAR = 0, 1, 2
 STENCIL_F32, STENCIL_F64, STENCIL_BF16 = 0, 1, 2
 STENCIL_PLAIN, STENCIL_BLOCKED, STENCIL_AUTO = 0, 1, 2
 STENCIL_HOST, STENCIL_DEVICE = 0, 1
-STENCIL_FIELD_ARRAY, STENCIL_COEF_ARRAY = 0, 1
+STENCIL_FIELD_ARRAY, STENCIL_COEF_ARRAY, STENCIL_GRAD_ARRAY = 0, 1, 2
 
 STATUS = {0: "STENCIL_OK", -1: "STENCIL_EINVAL", -2: "STENCIL_ENOSMEM", -3: "STENCIL_ETIMEOUT",
           -4: "STENCIL_ECUDA", -5: "STENCIL_EUNBOUND", -6: "STENCIL_ENOTSUP"}
@@ -60,6 +60,9 @@ SIGNATURES = [
     ("stencil_get_field", _I, [_H, _P, _I]),
     ("stencil_blocked_smem_bytes", ctypes.c_size_t, [_H, ctypes.POINTER(stencil_tuning)]),
     ("stencil_launch_count", _I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    ("stencil_adjoint_workspace_bytes", ctypes.c_size_t, [_H, _I, _I]),
+    ("stencil_run_checkpointed", _I, [_H, _I, _I, _P, ctypes.c_size_t]),
+    ("stencil_run_adjoint", _I, [_H, _I, _I, _P, _P, ctypes.POINTER(_P), _P, ctypes.c_size_t]),
     ("stencil_probe_fma", _I, [_I, _I, _P, _P, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]),
     ("stencil_sync", _I, [_H]),

@@ -2,6 +2,7 @@
 // the sweep kernels. Declarations and contracts are in include/stencil_gb300.h.
 #include <stdint.h>
 #include <string.h>
+#include <math.h>
 
 #include <new>
 
@@ -129,9 +130,10 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
 
 int stencil_layout_of(stencil_t h, int which, stencil_layout* out) {
     if (!h || !out) return STENCIL_EINVAL;
-    if (which != STENCIL_FIELD_ARRAY && which != STENCIL_COEF_ARRAY) return STENCIL_EINVAL;
-    if (which == STENCIL_COEF_ARRAY && h->kind == STENCIL_7PT_CONST) return STENCIL_EINVAL;
-    int eb = dtype_bytes(which == STENCIL_FIELD_ARRAY ? h->fdt : h->cdt);
+    if (which != STENCIL_FIELD_ARRAY && which != STENCIL_COEF_ARRAY && which != STENCIL_GRAD_ARRAY)
+        return STENCIL_EINVAL;
+    if (which != STENCIL_FIELD_ARRAY && h->kind == STENCIL_7PT_CONST) return STENCIL_EINVAL;
+    int eb = which == STENCIL_FIELD_ARRAY ? dtype_bytes(h->fdt) : (which == STENCIL_COEF_ARRAY ? dtype_bytes(h->cdt) : 8);
     out->radius = h->L.R;
     out->elem_bytes = eb;
     out->x_offset = h->L.xo;
@@ -279,6 +281,95 @@ int stencil_get_field(stencil_t h, void* dst, int where) {
     cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), dst, h->field[h->parity], false);
     if (e != cudaSuccess) return STENCIL_ECUDA;
     if (where == STENCIL_HOST) return from_cuda(cudaStreamSynchronize(h->stream));
+    return STENCIL_OK;
+}
+
+static int ckpt_k(int T, int ckpt_every) {
+    if (ckpt_every > 0) return ckpt_every;
+    int k = (int)ceil(sqrt((double)(T > 0 ? T : 1)));
+    return k < 1 ? 1 : k;
+}
+
+size_t stencil_adjoint_workspace_bytes(stencil_t h, int T, int ckpt_every) {
+    if (!h || T < 0) return 0;
+    int k = ckpt_k(T, ckpt_every);
+    int nck = T > 0 ? (T + k - 1) / k : 1;
+    return (size_t)(nck + k + 2) * h->L.count() * (size_t)dtype_bytes(h->fdt);
+}
+
+int stencil_run_checkpointed(stencil_t h, int T, int ckpt_every, void* workspace, size_t workspace_bytes) {
+    if (!h || T < 0 || !workspace) return STENCIL_EINVAL;
+    if (!h->bound) return STENCIL_EUNBOUND;
+    if (h->kind == STENCIL_7PT_CONST) return STENCIL_ENOTSUP;
+    if (workspace_bytes < stencil_adjoint_workspace_bytes(h, T, ckpt_every)) return STENCIL_EINVAL;
+    if (!aligned16(workspace)) return STENCIL_EINVAL;
+    const int k = ckpt_k(T, ckpt_every);
+    const int nck = T > 0 ? (T + k - 1) / k : 1;
+    const size_t fb = h->L.count() * (size_t)dtype_bytes(h->fdt);
+    char* ws = static_cast<char*>(workspace);
+    int done = 0;
+    for (int c = 0; c < nck; ++c) {
+        cudaError_t e = cudaMemcpyAsync(ws + (size_t)c * fb, h->field[h->parity], fb, cudaMemcpyDeviceToDevice,
+                                        h->stream);
+        if (e != cudaSuccess) return STENCIL_ECUDA;
+        int steps = (c + 1 < nck) ? k : T - done;
+        int rc = stencil_run(h, steps);
+        if (rc != STENCIL_OK) return rc;
+        done += steps;
+    }
+    return STENCIL_OK;
+}
+
+int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T, void* g_u0, void* const* g_coef,
+                        void* workspace, size_t workspace_bytes) {
+    if (!h || T < 0 || !lambda_T || !g_u0 || !g_coef || !workspace) return STENCIL_EINVAL;
+    if (!h->bound) return STENCIL_EUNBOUND;
+    if (h->kind == STENCIL_7PT_CONST) return STENCIL_ENOTSUP;
+    if (workspace_bytes < stencil_adjoint_workspace_bytes(h, T, ckpt_every)) return STENCIL_EINVAL;
+    const int nc = kind_ncoef(h->kind);
+    for (int m = 0; m < nc; ++m)
+        if (!g_coef[m] || !aligned16(g_coef[m])) return STENCIL_EINVAL;
+    if (!aligned16(workspace) || !aligned16(g_u0) || !aligned16(lambda_T)) return STENCIL_EINVAL;
+    const int k = ckpt_k(T, ckpt_every);
+    const int nck = T > 0 ? (T + k - 1) / k : 1;
+    const size_t cnt = h->L.count();
+    const size_t fb = cnt * (size_t)dtype_bytes(h->fdt);
+    char* ws = static_cast<char*>(workspace);
+    auto ckpt = [&](int c) { return (void*)(ws + (size_t)c * fb); };
+    auto state = [&](int j) { return (void*)(ws + (size_t)(nck + j) * fb); };  // j = 1 .. k-1 used
+    void* lam[2] = {ws + (size_t)(nck + k) * fb, ws + (size_t)(nck + k + 1) * fb};
+    SweepArgs a = args_of(h);
+    cudaStream_t s = h->stream;
+    cudaError_t e;
+    double* gC[13] = {};
+    for (int m = 0; m < nc; ++m) {
+        gC[m] = static_cast<double*>(g_coef[m]);
+        if ((e = fill_value(gC[m], cnt, DT_F64, 0.0, s)) != cudaSuccess) return STENCIL_ECUDA;
+        ++h->launches;
+    }
+    if ((e = fill_value(lam[1], cnt, h->fdt, 0.0, s)) != cudaSuccess) return STENCIL_ECUDA;
+    if ((e = copy_interior_zero_halo(h->L, h->fdt, lambda_T, lam[0], s)) != cudaSuccess) return STENCIL_ECUDA;
+    h->launches += 2;
+    // in-segment states inherit the Dirichlet halo of u_0
+    for (int j = 1; j < k; ++j)
+        if (cudaMemcpyAsync(state(j), ckpt(0), fb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return STENCIL_ECUDA;
+    int cur = 0;
+    for (int c = nck - 1; c >= 0 && T > 0; --c) {
+        const int t0 = c * k;
+        const int t1 = (t0 + k < T) ? t0 + k : T;
+        auto st = [&](int j) { return j == 0 ? ckpt(c) : state(j); };
+        for (int j = 1; j < t1 - t0; ++j) {
+            if ((e = plain_step(a, st(j - 1), st(j), s)) != cudaSuccess) return STENCIL_ECUDA;
+            ++h->launches;
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            if ((e = adjoint_step(a, lam[cur], st(t - t0), lam[cur ^ 1], gC, true, s)) != cudaSuccess)
+                return STENCIL_ECUDA;
+            ++h->launches;
+            cur ^= 1;
+        }
+    }
+    if (cudaMemcpyAsync(g_u0, lam[cur], fb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return STENCIL_ECUDA;
     return STENCIL_OK;
 }
 

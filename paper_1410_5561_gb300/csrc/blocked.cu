@@ -149,8 +149,9 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
     const int k = P.row;
     const int b = P.bmin + (int)blockIdx.y;
     const int a = b + k;
-    const int D = P.D, Q = P.Q, Xs = P.Xs, Xt = P.Xt, EH = P.EH;
+    const int D = P.D, Xs = P.Xs, Xt = P.Xt, EH = P.EH;
     constexpr int d = NF + R;
+    constexpr int Q = 3 * NF + 2 * R;  // ring depth (planes per level)
     const int x0 = (int)blockIdx.x * Xt;
     const int Ny = L.ny, Nz = L.nz, Nx = L.nx;
     const int rnx = ((Nx + V - 1) / V) * V;
@@ -296,7 +297,12 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
                 }
             }
         }
-        // Dirichlet z-halo planes: every row of the level's ring
+        // Dirichlet z-halo planes: every row of the level's ring (only in the first
+        // and last few steps of the wavefront)
+        const int zb_hi = s * NF + NF + R, zb_lo = zb_hi - (Lt - 1) * d;
+        const bool near_lo = zb_lo < 0 && zb_hi + NF > -R;
+        const bool near_hi = zb_hi + NF > Nz && zb_lo < Nz + R;
+        if (near_lo || near_hi)
         for (int l = 0; l < Lt; ++l) {
             const int zb = s * NF - l * d + NF + R;
             if (zb + NF <= -R || zb >= Nz + R || (zb >= 0 && zb + NF <= Nz)) continue;

@@ -43,6 +43,14 @@ cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s);
 cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T,
                         const BlockedTune& tune, cudaStream_t s, long long* launches);
 
+// One adjoint step: lam_out = A^T lam_in over the interior; if accumulate,
+// gC[m] += lam_in * (field value multiplying C_m) in FP64.
+cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, const void* u, void* lam_out, double* const* gC,
+                         bool accumulate, cudaStream_t s);
+
+// dst = src on the interior, 0 on every other cell (FP32 / FP64).
+cudaError_t copy_interior_zero_halo(const Layout& L, int dt, const void* src, void* dst, cudaStream_t s);
+
 // Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);
 

@@ -156,6 +156,41 @@ class Stencil:
     def run(self, T: int):
         C.call("stencil_run", self._h, int(T))
 
+    # ------------------------------------------------------------ adjoint
+    def adjoint_workspace(self, T: int, ckpt_every: int = 0) -> torch.Tensor:
+        """Device workspace for run_checkpointed / run_adjoint (reused when large enough)."""
+        need = int(C.lib().stencil_adjoint_workspace_bytes(self._h, int(T), int(ckpt_every)))
+        ws = getattr(self, "_adj_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 16), dtype=torch.uint8, device=self.device)
+            self._adj_ws = ws
+        return ws
+
+    def run_checkpointed(self, T: int, ckpt_every: int, workspace: torch.Tensor):
+        C.call("stencil_run_checkpointed", self._h, int(T), int(ckpt_every), _ptr(workspace),
+               ctypes.c_size_t(workspace.numel() * workspace.element_size()))
+
+    def run_adjoint(self, T: int, ckpt_every: int, lam_T: torch.Tensor, g_u0: torch.Tensor, g_coef,
+                    workspace: torch.Tensor):
+        """lam_T, g_u0: field-layout tensors (self.padded shape); g_coef: FP64 gradient-layout tensors."""
+        arr = (ctypes.c_void_p * 13)(*[g.data_ptr() for g in g_coef])
+        C.call("stencil_run_adjoint", self._h, int(T), int(ckpt_every), _ptr(lam_T), _ptr(g_u0), arr,
+               _ptr(workspace), ctypes.c_size_t(workspace.numel() * workspace.element_size()))
+
+    def new_field_array(self, zero: bool = True) -> torch.Tensor:
+        n = self.layout.bytes // self.layout.elem_bytes
+        return torch.zeros(n, dtype=self.dtype, device=self.device) if zero else \
+            torch.empty(n, dtype=self.dtype, device=self.device)
+
+    def new_grad_array(self) -> torch.Tensor:
+        return torch.empty(self.layout.bytes // self.layout.elem_bytes, dtype=torch.float64, device=self.device)
+
+    def interior_of(self, t: torch.Tensor) -> torch.Tensor:
+        """Interior view of any array in this grid's element layout (field, coefficient or gradient)."""
+        lay = self.layout
+        r, xo = lay.radius, lay.x_offset
+        return t.view(lay.planes, lay.pitch_y, lay.pitch_x)[r:r + self.nz, r:r + self.ny, xo:xo + self.nx]
+
     @property
     def launches(self) -> int:
         """Kernels this grid has launched so far."""

@@ -20,7 +20,7 @@
 //   diamond run as one thread-block cluster that advances in lockstep (an
 //   execution-only barrier per step), which orders a neighbour's HBM store
 //   after the loads of the same (parity-array) cells in its overlap.
-// * Each time level l keeps a ring of Q = 3 N_F + 2R planes in shared memory
+// * Each time level l keeps a ring of Q = 3 N_F + R (R = 4: 3 N_F + 2R) planes in shared memory
 //   holding u_{t_l} on rows N_l = Yc(t_l) +- R. Level l computes planes
 //   [s N_F - l d, s N_F - l d + N_F) at step s with d = N_F + R, so the levels
 //   of one step are independent and one __syncthreads per step suffices.
@@ -122,7 +122,6 @@ struct Item {
     int zb0;          // z of the item's first plane at step 0 (= -l d)
     int qr;           // vectors available to the right of this lane's vector
     int xg;           // interior x of the lane's element 0
-    int wz;           // plane the register window is positioned at (-inf: reload)
     bool valid, active, indom, full, store;
 };
 
@@ -151,7 +150,9 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
     const int a = b + k;
     const int D = P.D, Xs = P.Xs, Xt = P.Xt, EH = P.EH;
     constexpr int d = NF + R;
-    constexpr int Q = 3 * NF + 2 * R;  // ring depth (planes per level)
+    // ring depth (planes per level): with register windows the ring is read from the
+    // current plane up, otherwise from R planes below it
+    constexpr int Q = PERSIST ? 3 * NF + R : 3 * NF + 2 * R;
     const int x0 = (int)blockIdx.x * Xt;
     const int Ny = L.ny, Nz = L.nz, Nx = L.nx;
     const int rnx = ((Nx + V - 1) / V) * V;
@@ -245,7 +246,6 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
         Item<TF, V>& I = it[kk];
         const int id = warp + kk * NW;
         I.valid = id < M.nitem;
-        I.wz = -(1 << 30);
         if (!I.valid) continue;
         const int l = M.il[id], y = M.iy[id];
         const int nlo = M.nlo[l];
@@ -268,6 +268,15 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
         I.g0 = I.indom ? L.at(I.xg, y, 0) : 0;
         I.gdst = P.f[(P.p0 + M.t0 + l + 1) & 1];
         I.zb0 = -l * d;
+    }
+
+    if constexpr (PERSIST) {
+#pragma unroll
+        for (int kk = 0; kk < K; ++kk)
+#pragma unroll
+            for (int r = 0; r < WIN; ++r)
+#pragma unroll
+                for (int e = 0; e < V; ++e) win[kk][r].v[e] = hv;
     }
 
     // ---- producer: HBM loads (cp.async) and Dirichlet fills of planes P_l(s) = [s NF - l d + NF + R, +NF)
@@ -336,26 +345,44 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
             Item<TF, V>& I = it[kk];
             if (!I.valid) continue;
             const int zb = s * NF + I.zb0;
-            const int zfirst = zb < 0 ? 0 : zb;
-            const int zlast = zb + NF < Nz ? zb + NF : Nz;
-            if (zfirst >= zlast) continue;  // warp-uniform
-            int sl = pmod(zfirst - R, Q);   // slot of plane zfirst - R
-            if (!PERSIST || I.wz != zfirst) {
+            int zfirst, zlast, sl = 0, sc = 0;
+            if constexpr (PERSIST) {
+                // the window advances every step from the start; planes below 0 are the
+                // Dirichlet value, so the ring is never read below the current plane
+                if (zb + NF + R <= 0 || zb >= Nz) continue;  // warp-uniform
+                zfirst = zb;
+                zlast = zb + NF;
+            } else {
+                zfirst = zb < 0 ? 0 : zb;
+                zlast = zb + NF < Nz ? zb + NF : Nz;
+                if (zfirst >= zlast) continue;  // warp-uniform
+                sl = pmod(zfirst - R, Q);       // slot of plane zfirst - R
 #pragma unroll
                 for (int r = 0; r < 2 * R; ++r) {
                     win[kk][r] = ldv<TF, V>(I.rowp + sl * I.PS);
                     sl = wrap_inc(sl, Q);
                 }
-            } else {
-                sl += 2 * R;
-                if (sl >= Q) sl -= Q;
+                sc = sl - R < 0 ? sl - R + Q : sl - R;  // slot of plane zfirst
             }
-            int sc = sl - R < 0 ? sl - R + Q : sl - R;  // slot of plane zfirst
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
                 const int z = zfirst + f;
-                if (z < zlast) {
-                    win[kk][2 * R + f] = ldv<TF, V>(I.rowp + sl * I.PS);  // plane z + R
+                bool live;
+                if constexpr (PERSIST) {
+                    const int pz = z + R;  // newest plane of the window
+                    if (pz >= 0 && z < Nz) {
+                        win[kk][2 * R + f] = ldv<TF, V>(I.rowp + (pz % Q) * I.PS);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) win[kk][2 * R + f].v[e] = hv;
+                    }
+                    live = z >= 0 && z < Nz;
+                    sc = live ? z % Q : 0;
+                } else {
+                    live = z < zlast;
+                    if (live) win[kk][2 * R + f] = ldv<TF, V>(I.rowp + sl * I.PS);  // plane z + R
+                }
+                if (live) {
                     const VT& ctr = win[kk][f + R];
                     const TF* cp = I.rowp + sc * I.PS;
                     TF xl[(2 * J + 1) * V];
@@ -443,15 +470,17 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
                                 if (I.xg + e < Nx) I.gdst[gidx + e] = out.v[e];
                         }
                     }
-                    sl = wrap_inc(sl, Q);
-                    sc = wrap_inc(sc, Q);
+                    if constexpr (!PERSIST) {
+                        sl = wrap_inc(sl, Q);
+                        sc = wrap_inc(sc, Q);
+                    }
                 }
             }
-            if (PERSIST) {
+            if constexpr (PERSIST) {
 #pragma unroll
                 for (int r = 0; r < 2 * R; ++r) win[kk][r] = win[kk][r + NF];
-                I.wz = (zlast - zfirst == NF) ? zfirst + NF : -(1 << 30);
             }
+            (void)zlast;
         }
         cp_async_wait_1();
         __syncthreads();
@@ -508,7 +537,7 @@ static BlkShape blk_shape(const SweepArgs& a, const BlockedTune& tn) {
     s.Xt = tn.xtile;
     s.EH = ((R * ltmax + s.V - 1) / s.V) * s.V + s.HV;
     s.Xs = s.Xt + 2 * s.EH;
-    s.Q = 3 * tn.nf + 2 * R;
+    s.Q = R == 1 ? 3 * tn.nf + R : 3 * tn.nf + 2 * R;  // matches the kernel's ring depth
     s.smem = (size_t)s.Q * ring_rows_bound(tn.dw, R) * s.Xs * eb;
     s.ok = true;
     return s;

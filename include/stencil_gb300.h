@@ -179,6 +179,60 @@ int stencil_launch_count(stencil_t h, long long* out);
  * per FMA). scratch: device buffer of at least 65536 bytes. Synchronous. */
 int stencil_probe_fma(int dtype, int iters, void* scratch, void* cuda_stream, double* seconds, double* flops);
 
+/* ---- Batch: many independent grids advanced by one persistent launch.
+ * Every grid runs the blocked schedule (Section II-A) with one tile covering
+ * its whole x extent; tiles of all grids sit in one dependency-ordered list
+ * and the CTAs of one persistent kernel pop them from an atomic counter, each
+ * waiting (with a bounded spin) until the diamonds below it have published
+ * their results: the GPU form of the paper's queue of ready diamond tiles. */
+typedef struct stencil_batch* stencil_batch_t; /* opaque, owned by the library */
+
+/* Plan a batch: grids[q] (bound, same kind and dtypes) advances by T[q] >= 0 steps
+ * per launch. tuning: dw, nf (1 or 2) and warps are used for every grid; xtile is
+ * ignored. STENCIL_EINVAL if a grid cannot use the tuning. */
+int stencil_batch_create(stencil_batch_t* out, const stencil_t* grids, const int* T, int n,
+                         const stencil_tuning* tuning);
+
+/* Device workspace bytes the batch needs (descriptors, tile list, counters). */
+size_t stencil_batch_workspace_bytes(stencil_batch_t b);
+
+/* Number of tiles one launch processes. */
+int stencil_batch_item_count(stencil_batch_t b);
+
+/* Upload the plan into workspace (device, caller-owned, 16-byte aligned,
+ * stencil_batch_workspace_bytes long); synchronous on cuda_stream. The grids'
+ * current parities are recorded here. */
+int stencil_batch_bind(stencil_batch_t b, void* workspace, void* cuda_stream);
+
+/* Enqueue one launch (a counter reset and the persistent kernel) on cuda_stream;
+ * it can be captured in a CUDA graph. Each grid advances by its T; the handles'
+ * parities are updated by this call. Replays of a captured graph advance the
+ * grids again without passing through this call: afterwards call
+ * stencil_batch_sync_parity before using the grids. */
+int stencil_batch_launch(stencil_batch_t b, void* cuda_stream);
+
+/* Kernels this batch has enqueued so far. */
+int stencil_batch_launch_count(stencil_batch_t b, long long* out);
+
+/* Status of the last launch (synchronous): *status = STENCIL_OK, or
+ * STENCIL_ETIMEOUT when a dependency wait gave up (the grids' contents are then
+ * undefined). */
+int stencil_batch_status(stencil_batch_t b, int* status);
+
+/* Copy the device-side parities (which array holds each grid's current time
+ * level) into the grid handles. Synchronous. */
+int stencil_batch_sync_parity(stencil_batch_t b);
+
+/* Bound on the spin iterations of a dependency wait (about 0.2 us each; the
+ * default, 2^24, is a few seconds). */
+int stencil_batch_set_wait_limit(stencil_batch_t b, unsigned spins);
+
+/* Test hook: make tile `item` wait on a completion flag that no tile ever sets,
+ * so that its wait runs out and the launch reports STENCIL_ETIMEOUT. */
+int stencil_batch_inject_stall(stencil_batch_t b, int item);
+
+int stencil_batch_destroy(stencil_batch_t b);
+
 /* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error. */
 int stencil_sync(stencil_t h);
 

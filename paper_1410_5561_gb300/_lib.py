@@ -65,6 +65,18 @@ SIGNATURES = [
     ("stencil_run_adjoint", _I, [_H, _I, _I, _P, _P, ctypes.POINTER(_P), _P, ctypes.c_size_t]),
     ("stencil_probe_fma", _I, [_I, _I, _P, _P, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(ctypes.c_double)]),
+    ("stencil_batch_create", _I, [ctypes.POINTER(_H), ctypes.POINTER(_H), ctypes.POINTER(_I), _I,
+                                  ctypes.POINTER(stencil_tuning)]),
+    ("stencil_batch_workspace_bytes", ctypes.c_size_t, [_H]),
+    ("stencil_batch_item_count", _I, [_H]),
+    ("stencil_batch_bind", _I, [_H, _P, _P]),
+    ("stencil_batch_launch", _I, [_H, _P]),
+    ("stencil_batch_launch_count", _I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    ("stencil_batch_status", _I, [_H, ctypes.POINTER(_I)]),
+    ("stencil_batch_sync_parity", _I, [_H]),
+    ("stencil_batch_set_wait_limit", _I, [_H, ctypes.c_uint]),
+    ("stencil_batch_inject_stall", _I, [_H, _I]),
+    ("stencil_batch_destroy", _I, [_H]),
     ("stencil_sync", _I, [_H]),
     ("stencil_strerror", ctypes.c_char_p, [_I]),
     ("stencil_destroy", _I, [_H]),

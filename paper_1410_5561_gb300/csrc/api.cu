@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include <new>
+#include <vector>
 
 #include "../../include/stencil_gb300.h"
 #include "internal.h"
@@ -382,6 +383,125 @@ size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning) {
 int stencil_launch_count(stencil_t h, long long* out) {
     if (!h || !out) return STENCIL_EINVAL;
     *out = h->launches;
+    return STENCIL_OK;
+}
+
+// ------------------------------------------------------------------ batch
+
+struct stencil_batch {
+    std::vector<stencil_t> grids;
+    std::vector<int> T;
+    BlockedTune tn;
+    BatchLaunch bl;
+    bool bound = false;
+    cudaStream_t stream = nullptr;
+    long long launches = 0;
+};
+
+static void batch_grids(const stencil_batch* b, std::vector<BatchGrid>& g) {
+    g.resize(b->grids.size());
+    for (size_t q = 0; q < b->grids.size(); ++q) {
+        const stencil_grid* h = b->grids[q];
+        g[q].a = args_of(h);
+        g[q].field[0] = h->field[0];
+        g[q].field[1] = h->field[1];
+        g[q].parity = h->parity;
+        g[q].T = b->T[q];
+    }
+}
+
+int stencil_batch_create(stencil_batch_t* out, const stencil_t* grids, const int* T, int n,
+                         const stencil_tuning* tuning) {
+    if (!out || !grids || !T || n < 1 || !tuning) return STENCIL_EINVAL;
+    *out = nullptr;
+    for (int q = 0; q < n; ++q) {
+        if (!grids[q] || T[q] < 0) return STENCIL_EINVAL;
+        if (!grids[q]->bound) return STENCIL_EUNBOUND;
+    }
+    stencil_batch* b = new (std::nothrow) stencil_batch();
+    if (!b) return STENCIL_EINVAL;
+    b->grids.assign(grids, grids + n);
+    b->T.assign(T, T + n);
+    b->tn = BlockedTune{tuning->dw, tuning->nf, tuning->warps, 0};
+    std::vector<BatchGrid> g;
+    batch_grids(b, g);
+    cudaError_t e = batch_plan(g.data(), n, b->tn, &b->bl);
+    if (e != cudaSuccess) {
+        delete b;
+        return STENCIL_EINVAL;
+    }
+    *out = b;
+    return STENCIL_OK;
+}
+
+size_t stencil_batch_workspace_bytes(stencil_batch_t b) { return b ? b->bl.bytes : 0; }
+
+int stencil_batch_item_count(stencil_batch_t b) { return b ? b->bl.nitems : STENCIL_EINVAL; }
+
+int stencil_batch_bind(stencil_batch_t b, void* workspace, void* cuda_stream) {
+    if (!b || !workspace || !aligned16(workspace)) return STENCIL_EINVAL;
+    std::vector<BatchGrid> g;
+    batch_grids(b, g);
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    if (batch_upload(g.data(), (int)g.size(), b->tn, &b->bl, workspace, b->stream) != cudaSuccess)
+        return STENCIL_ECUDA;
+    b->bound = true;
+    return STENCIL_OK;
+}
+
+int stencil_batch_launch(stencil_batch_t b, void* cuda_stream) {
+    if (!b) return STENCIL_EINVAL;
+    if (!b->bound) return STENCIL_EUNBOUND;
+    if (batch_launch(b->bl, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return STENCIL_ECUDA;
+    b->launches += 2;  // counter reset + persistent kernel
+    for (size_t q = 0; q < b->grids.size(); ++q) b->grids[q]->parity = (b->grids[q]->parity + b->T[q]) & 1;
+    return STENCIL_OK;
+}
+
+int stencil_batch_launch_count(stencil_batch_t b, long long* out) {
+    if (!b || !out) return STENCIL_EINVAL;
+    *out = b->launches;
+    return STENCIL_OK;
+}
+
+int stencil_batch_status(stencil_batch_t b, int* status) {
+    if (!b || !status) return STENCIL_EINVAL;
+    if (!b->bound) return STENCIL_EUNBOUND;
+    int v = 0;
+    if (cudaMemcpy(&v, b->bl.ws + b->bl.off_counters + sizeof(int), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return STENCIL_ECUDA;
+    *status = v == 0 ? STENCIL_OK : STENCIL_ETIMEOUT;
+    return STENCIL_OK;
+}
+
+int stencil_batch_sync_parity(stencil_batch_t b) {
+    if (!b) return STENCIL_EINVAL;
+    if (!b->bound) return STENCIL_EUNBOUND;
+    std::vector<int> par(b->grids.size());
+    if (cudaMemcpy(par.data(), b->bl.ws + b->bl.off_parity, sizeof(int) * par.size(), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return STENCIL_ECUDA;
+    for (size_t q = 0; q < par.size(); ++q) b->grids[q]->parity = par[q] & 1;
+    return STENCIL_OK;
+}
+
+int stencil_batch_set_wait_limit(stencil_batch_t b, unsigned spins) {
+    if (!b || spins == 0) return STENCIL_EINVAL;
+    b->bl.spin_limit = spins;
+    return STENCIL_OK;
+}
+
+int stencil_batch_inject_stall(stencil_batch_t b, int item) {
+    if (!b || item < 0 || item >= b->bl.nitems) return STENCIL_EINVAL;
+    if (!b->bound) return STENCIL_EUNBOUND;
+    b->bl.items[item].dep[2] = b->bl.nitems;  // the extra completion flag, which no tile ever sets
+    if (batch_reupload_items(&b->bl, b->stream) != cudaSuccess) return STENCIL_ECUDA;
+    return STENCIL_OK;
+}
+
+int stencil_batch_destroy(stencil_batch_t b) {
+    if (!b) return STENCIL_EINVAL;
+    delete b;
     return STENCIL_OK;
 }
 

@@ -35,6 +35,8 @@
 //   (or t = T-1). Coefficients are read through L2.
 // * The per-point arithmetic is the shared update of common.cuh, so results
 //   are bit-identical to the plain sweep.
+#include <vector>
+
 #include "internal.h"
 
 namespace stg {
@@ -56,16 +58,25 @@ struct TileMeta {
     int ldlo[MAXLV], ldhi[MAXLV];      // ring vectors loaded for this level's input
     short tl[MAXTASK], ty[MAXTASK];    // load / fill tasks for interior planes
     unsigned char tfill[MAXTASK];
-    short il[MAXITEM], iy[MAXITEM];    // compute items (level, row)
+    short il[MAXITEM], iy[MAXITEM];    // compute items (level, row, 32-vector chunk)
+    unsigned char ich[MAXITEM];
 };
 
+// Per-grid constants of a blocked sweep.
 template <typename TF, typename TC>
-struct BlkParams {
+struct GridArgs {
     Layout L;
     TF* f[2];
     const TC* C[13];
     TF c0, c1, halo;
-    int p0, T, D, row, bmin, Xt, EH, Q, Xs, CX;
+    int p0, T, D, Xt, EH, Xs, CX;
+};
+
+// Row launch: every tile (row, bmin + blockIdx.y) of one diamond row, x tile blockIdx.x.
+template <typename TF, typename TC>
+struct BlkParams {
+    GridArgs<TF, TC> G;
+    int row, bmin;
 };
 
 __host__ __device__ inline void level_rows(int D, int R, int Ny, int a, int b, int t, int& lo, int& hi) {
@@ -125,8 +136,12 @@ struct Item {
     bool valid, active, indom, full, store;
 };
 
+// One tile (row k, diamond b) of one grid, x tile xti, all z; the whole CTA
+// participates. lock: the x tiles of the diamond run as a lockstep cluster.
+// p0: array holding u_0 of this run. ring / M: the CTA's shared memory.
 template <int KIND, typename TF, typename TC, int K, int NF>
-__global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF, TC> P) {
+__device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k, const int b, const int xti,
+                                         const bool lock, const int p0, TileMeta& M, TF* ring) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int NC = KindTraits<KIND>::NC;
     constexpr int V = 16 / sizeof(TF);
@@ -136,25 +151,20 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
     constexpr int WIN = 2 * R + NF;
     using VT = Vec<TF, V>;
 
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ TileMeta M;
-    TF* ring = reinterpret_cast<TF*>(smem_raw);
-
     const Layout& L = P.L;
     const int tid = threadIdx.x;
     const int NT = blockDim.x;
     const int NW = NT >> 5;
     const int warp = tid >> 5, lane = tid & 31;
-    const int k = P.row;
-    const int b = P.bmin + (int)blockIdx.y;
     const int a = b + k;
     const int D = P.D, Xs = P.Xs, Xt = P.Xt, EH = P.EH;
     constexpr int d = NF + R;
     // ring depth (planes per level): with register windows the ring is read from the
     // current plane up, otherwise from R planes below it
     constexpr int Q = PERSIST ? 3 * NF + R : 3 * NF + 2 * R;
-    const int x0 = (int)blockIdx.x * Xt;
+    const int x0 = xti * Xt;
     const int Ny = L.ny, Nz = L.nz, Nx = L.nx;
+    __syncthreads();  // the previous tile of this CTA has finished with M and the ring
     const int rnx = ((Nx + V - 1) / V) * V;
     const int nvs = Xs / V;  // vectors per ring row
 
@@ -207,11 +217,14 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
                     M.tfill[ntask] = halo_row ? 1 : 0;
                     ++ntask;
                 }
-                for (int y = lo; y < hi && nitem < MAXITEM; ++y) {
-                    M.il[nitem] = (short)l;
-                    M.iy[nitem] = (short)y;
-                    ++nitem;
-                }
+                const int nch = (cdiv(xh - x0 + EH, V) - M.vlo[l] + 31) / 32;
+                for (int y = lo; y < hi; ++y)
+                    for (int c = 0; c < nch && nitem < MAXITEM; ++c) {
+                        M.il[nitem] = (short)l;
+                        M.iy[nitem] = (short)y;
+                        M.ich[nitem] = (unsigned char)c;
+                        ++nitem;
+                    }
             }
         }
         M.ntask = ntask;
@@ -250,7 +263,7 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
         const int l = M.il[id], y = M.iy[id];
         const int nlo = M.nlo[l];
         I.PS = (M.nhi[l] - nlo) * Xs;
-        const int v = M.vlo[l] + lane;
+        const int v = M.vlo[l] + 32 * M.ich[id] + lane;
         const int vr = v < nvs ? v : nvs - 1;  // clamped read vector (inactive lanes only)
         I.qr = nvs - 1 - vr;
         I.rowp = ring + M.roff[l] + (y - nlo) * Xs + vr * V;
@@ -266,7 +279,7 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
         }
         I.store = I.active && I.indom && !(y >= M.wlo[l] && y < M.whi[l]) && I.xg >= x0 && I.xg < x0 + Xt;
         I.g0 = I.indom ? L.at(I.xg, y, 0) : 0;
-        I.gdst = P.f[(P.p0 + M.t0 + l + 1) & 1];
+        I.gdst = P.f[(p0 + M.t0 + l + 1) & 1];
         I.zb0 = -l * d;
     }
 
@@ -292,7 +305,7 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
             TF* rowr = ring + M.roff[l] + (y - nlo) * Xs;
             const int ldlo = M.ldlo[l], ldhi = M.ldhi[l];
             const int zb = s * NF - l * d + NF + R;
-            const TF* src = fill ? nullptr : P.f[(P.p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH);
+            const TF* src = fill ? nullptr : P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH);
 #pragma unroll
             for (int fz = 0; fz < NF; ++fz) {
                 const int z = zb + fz;
@@ -328,7 +341,6 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
         }
     };
 
-    const bool lock = P.CX > 1;
     produce(s_begin);
     cp_async_commit();
     if (lock) cluster_arrive_relaxed();
@@ -490,6 +502,97 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF
     cp_async_wait_all();
 }
 
+template <int KIND, typename TF, typename TC, int K, int NF>
+__global__ void __launch_bounds__(BLK_MAXT, 1) blocked_kernel(const BlkParams<TF, TC> P) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ TileMeta M;
+    run_tile<KIND, TF, TC, K, NF>(P.G, P.row, P.bmin + (int)blockIdx.y, (int)blockIdx.x, P.G.CX > 1, P.G.p0, M,
+                                  reinterpret_cast<TF*>(smem_raw));
+}
+
+
+// ------------------------------------------------------------- persistent batch
+// Many independent grids in one launch. Every tile (grid g, row k, diamond b)
+// covers its grid's whole x extent. Tiles are listed in row order; a CTA pops
+// the next tile from an atomic counter and waits (bounded) until the tiles it
+// depends on have published their results: (g, k-1, b), (g, k-1, b+1) and
+// (g, k-2, b+1) (the last one matters only when the first two are empty). This
+// is the GPU form of the paper's queue of ready diamonds (Section II-A). Every
+// popped tile is held by a running CTA and waits only on earlier tiles, so the
+// persistent grid (at most the co-resident CTAs) cannot deadlock; a wait that
+// exceeds its limit sets the status word and the CTA leaves the loop.
+
+template <typename TF, typename TC>
+struct BatchArgs {
+    const GridArgs<TF, TC>* grids;  // per grid
+    const BatchItem* items;         // dependency order
+    int nitems;
+    int* head;         // next item to pop
+    int* status;       // 0 ok, 1 a dependency wait gave up
+    int* done;         // per item: published
+    int* gdone;        // per grid: tiles finished in this launch
+    const int* ntiles; // per grid: tiles per launch
+    int* parity;       // per grid: array holding the current time level
+    unsigned spin_limit;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_gpu(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+template <int KIND, typename TF, typename TC, int K, int NF>
+__global__ void __launch_bounds__(BLK_MAXT, 1) blocked_batch_kernel(const BatchArgs<TF, TC> A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ TileMeta M;
+    __shared__ int s_item, s_abort, s_p0;
+    TF* ring = reinterpret_cast<TF*>(smem_raw);
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int i = atomicAdd(A.head, 1);
+            int abort = 0;
+            if (i < A.nitems) {
+                const BatchItem it = A.items[i];
+                for (int q = 0; q < 3 && !abort; ++q) {
+                    const int dd = it.dep[q];
+                    if (dd < 0) continue;
+                    unsigned n = 0;
+                    while (ld_acquire_gpu(A.done + dd) == 0) {
+                        if (++n > A.spin_limit || ld_volatile(A.status) != 0) {
+                            abort = 1;
+                            break;
+                        }
+                        __nanosleep(200);
+                    }
+                }
+                if (abort) atomicCAS(A.status, 0, 1);
+                s_p0 = ld_volatile(A.parity + it.g);
+            }
+            s_item = i;
+            s_abort = abort;
+        }
+        __syncthreads();
+        const int i = s_item;
+        if (i >= A.nitems || s_abort) break;
+        const BatchItem it = A.items[i];
+        const int p0 = s_p0;
+        run_tile<KIND, TF, TC, K, NF>(A.grids[it.g], it.k, it.b, 0, false, p0, M, ring);
+        __threadfence();  // this thread's HBM stores of the tile are visible GPU-wide
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st_release_gpu(A.done + i, 1);
+            if (atomicAdd(A.gdone + it.g, 1) == A.ntiles[it.g] - 1)
+                A.parity[it.g] = (p0 + A.grids[it.g].T) & 1;  // every tile of g has read p0
+        }
+    }
+}
+
 // ------------------------------------------------------------------- host side
 
 static int ring_rows_bound(int D, int R) {
@@ -506,47 +609,74 @@ static int ring_rows_bound(int D, int R) {
 static int item_bound(int D, int R) { return D * D / (2 * R); }
 
 struct BlkShape {
-    int V, HV, Xt, EH, Xs, Q, K;
+    int V, HV, Xt, EH, Xs, Q, K, nch;
     size_t smem;
     bool ok;
 };
 
-static BlkShape blk_shape(const SweepArgs& a, const BlockedTune& tn) {
+// Shape of the rings and the work split for one grid and tuning. With xtile >= nx
+// the whole row is one tile (no cluster); rows wider than one warp of vectors are
+// split into 32-vector chunks, each one item.
+static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps, int xtile) {
     BlkShape s{};
-    int R = kind_radius(a.kind);
-    int eb = dtype_bytes(a.fdt);
+    int R = kind_radius(kind);
+    int eb = dtype_bytes(fdt);
     s.V = 16 / eb;
     int J = (R + s.V - 1) / s.V;
     s.HV = J * s.V;
     s.ok = false;
-    if (tn.dw < 2 * R || tn.dw % (2 * R) != 0) return s;
-    if (tn.nf < 1 || tn.nf > 2) return s;
-    int ltmax = tn.dw / R - 1;
+    if (dw < 2 * R || dw % (2 * R) != 0) return s;
+    if (nf < 1 || nf > 2) return s;
+    int ltmax = dw / R - 1;
     if (ltmax > MAXLV) return s;
-    if (tn.warps < 1 || tn.warps * 32 > BLK_MAXT) return s;
-    if (tn.xtile < s.V || tn.xtile % s.V != 0 || tn.xtile > 4096) return s;
-    if ((a.L.nx + tn.xtile - 1) / tn.xtile > MAXCLUSTER) return s;
-    // one warp of vectors covers a tile row plus its trapezoid overlap at every level
+    if (warps < 1 || warps * 32 > BLK_MAXT) return s;
+    if (xtile < s.V || xtile % s.V != 0 || xtile > 4096) return s;
+    if ((nx + xtile - 1) / xtile > MAXCLUSTER) return s;
     int ov = ltmax > 1 ? (R * (ltmax - 1) + s.V - 1) / s.V : 0;
-    if (tn.xtile / s.V + 2 * ov > 32) return s;
-    int items = item_bound(tn.dw, R);
+    s.nch = (xtile / s.V + 2 * ov + 31) / 32;
+    int items = item_bound(dw, R) * s.nch;
     if (items > MAXITEM) return s;
-    int K = (items + tn.warps - 1) / tn.warps;
+    int K = (items + warps - 1) / warps;
     if (K > 4) return s;
     s.K = K <= 1 ? 1 : (K <= 2 ? 2 : 4);
-    s.Xt = tn.xtile;
+    s.Xt = xtile;
     s.EH = ((R * ltmax + s.V - 1) / s.V) * s.V + s.HV;
     s.Xs = s.Xt + 2 * s.EH;
-    s.Q = R == 1 ? 3 * tn.nf + R : 3 * tn.nf + 2 * R;  // matches the kernel's ring depth
-    s.smem = (size_t)s.Q * ring_rows_bound(tn.dw, R) * s.Xs * eb;
+    s.Q = R == 1 ? 3 * nf + R : 3 * nf + 2 * R;  // matches the kernel's ring depth
+    s.smem = (size_t)s.Q * ring_rows_bound(dw, R) * s.Xs * eb;
     s.ok = true;
     return s;
+}
+
+static BlkShape blk_shape(const SweepArgs& a, const BlockedTune& tn) {
+    return blk_shape_x(a.kind, a.fdt, a.L.nx, tn.dw, tn.nf, tn.warps, tn.xtile);
 }
 
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tn) {
     BlkShape s = blk_shape(a, tn);
     if (!s.ok) return 0;
     return s.smem + sizeof(TileMeta);
+}
+
+template <typename TF, typename TC>
+static GridArgs<TF, TC> grid_args(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
+                                  const BlkShape& sh) {
+    GridArgs<TF, TC> G{};
+    G.L = a.L;
+    G.f[0] = static_cast<TF*>(field[0]);
+    G.f[1] = static_cast<TF*>(field[1]);
+    for (int m = 0; m < kind_ncoef(a.kind); ++m) G.C[m] = static_cast<const TC*>(a.coef[m]);
+    G.c0 = (TF)a.c0;
+    G.c1 = (TF)a.c1;
+    G.halo = (TF)a.halo;
+    G.p0 = p0;
+    G.T = T;
+    G.D = tn.dw;
+    G.Xt = sh.Xt;
+    G.EH = sh.EH;
+    G.Xs = sh.Xs;
+    G.CX = 1;
+    return G;
 }
 
 template <int KIND, typename TF, typename TC, int K, int NF>
@@ -562,21 +692,8 @@ static cudaError_t launch_blocked_k(const SweepArgs& a, void* const field[2], in
         if (e != cudaSuccess) return e;
     }
     BlkParams<TF, TC> P{};
-    P.L = a.L;
-    P.f[0] = static_cast<TF*>(field[0]);
-    P.f[1] = static_cast<TF*>(field[1]);
-    for (int m = 0; m < KindTraits<KIND>::NC; ++m) P.C[m] = static_cast<const TC*>(a.coef[m]);
-    P.c0 = (TF)a.c0;
-    P.c1 = (TF)a.c1;
-    P.halo = (TF)a.halo;
-    P.p0 = p0;
-    P.T = T;
-    P.D = tn.dw;
-    P.Xt = sh.Xt;
-    P.EH = sh.EH;
-    P.Q = sh.Q;
-    P.Xs = sh.Xs;
-    P.CX = nxt;
+    P.G = grid_args<TF, TC>(a, field, p0, T, tn, sh);
+    P.G.CX = nxt;
     const int D = tn.dw, Ny = a.L.ny;
     for (int k = 0;; ++k) {
         int tlo, thi;
@@ -658,6 +775,240 @@ cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T,
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
                 return launch_blocked<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, s, launches);
             if (a.fdt == DT_F64) return launch_blocked<K25V, double, double>(a, field, p0, T, tn, s, launches);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+
+// ------------------------------------------------------------- batch host side
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename TF, typename TC>
+static size_t grid_args_bytes() { return sizeof(GridArgs<TF, TC>); }
+
+static size_t gridargs_size(int fdt, int cdt) {
+    if (fdt == DT_F64) return grid_args_bytes<double, double>();
+    if (cdt == DT_BF16) return grid_args_bytes<float, __nv_bfloat16>();
+    return grid_args_bytes<float, float>();
+}
+
+// Host plan: the items (in row order) and their dependencies.
+static int batch_items(const BatchGrid* g, int n, int dw, std::vector<BatchItem>& items, std::vector<int>& ntiles) {
+    const int R = kind_radius(g[0].a.kind);
+    items.clear();
+    ntiles.assign(n, 0);
+    // per grid, per row: [bmin, bmax] and the item index of bmin
+    std::vector<std::vector<int>> rbmin(n), rbmax(n), rbase(n);
+    int kmax = 0;
+    for (int q = 0; q < n; ++q) {
+        for (int k = 0;; ++k) {
+            int tlo, thi;
+            row_trange(dw, R, g[q].T, k, tlo, thi);
+            if (tlo >= g[q].T) break;
+            kmax = k > kmax ? k : kmax;
+        }
+    }
+    for (int q = 0; q < n; ++q) {
+        rbmin[q].assign(kmax + 1, 1);
+        rbmax[q].assign(kmax + 1, 0);
+        rbase[q].assign(kmax + 1, -1);
+    }
+    auto nonempty = [&](int q, int k, int b) {
+        int tlo, thi;
+        row_trange(dw, R, g[q].T, k, tlo, thi);
+        for (int t = tlo; t < thi; ++t) {
+            int lo, hi;
+            level_rows(dw, R, g[q].a.L.ny, b + k, b, t, lo, hi);
+            if (hi > lo) return true;
+        }
+        return false;
+    };
+    auto index_of = [&](int q, int k, int b) -> int {
+        if (k < 0 || k > kmax || rbase[q][k] < 0 || b < rbmin[q][k] || b > rbmax[q][k]) return -1;
+        return rbase[q][k] + (b - rbmin[q][k]);
+    };
+    for (int k = 0; k <= kmax; ++k) {
+        for (int q = 0; q < n; ++q) {
+            const int Ny = g[q].a.L.ny;
+            int tlo, thi;
+            row_trange(dw, R, g[q].T, k, tlo, thi);
+            if (tlo >= g[q].T || thi <= tlo) continue;
+            int bmin = 1 << 30, bmax = -(1 << 30);
+            for (int b = -(k + 2) / 2 - 2; b <= (2 * Ny / dw - k) / 2 + 2; ++b)
+                if (nonempty(q, k, b)) {
+                    bmin = b < bmin ? b : bmin;
+                    bmax = b > bmax ? b : bmax;
+                }
+            if (bmax < bmin) continue;
+            rbmin[q][k] = bmin;
+            rbmax[q][k] = bmax;
+            rbase[q][k] = (int)items.size();
+            for (int b = bmin; b <= bmax; ++b) {
+                BatchItem it{};
+                it.g = q;
+                it.k = k;
+                it.b = b;
+                it.dep[0] = index_of(q, k - 1, b);
+                it.dep[1] = index_of(q, k - 1, b + 1);
+                it.dep[2] = index_of(q, k - 2, b + 1);
+                items.push_back(it);
+                ntiles[q]++;
+            }
+        }
+    }
+    return (int)items.size();
+}
+
+cudaError_t batch_plan(const BatchGrid* g, int n, const BlockedTune& tn, BatchLaunch* bl) {
+    if (n < 1) return cudaErrorInvalidValue;
+    const SweepArgs& a0 = g[0].a;
+    int K = 1;
+    size_t smem = 0;
+    for (int q = 0; q < n; ++q) {
+        const SweepArgs& a = g[q].a;
+        if (a.kind != a0.kind || a.fdt != a0.fdt || a.cdt != a0.cdt) return cudaErrorInvalidValue;
+        const int V = 16 / dtype_bytes(a.fdt);
+        const int xt = ((a.L.nx + V - 1) / V) * V;
+        BlkShape sh = blk_shape_x(a.kind, a.fdt, a.L.nx, tn.dw, tn.nf, tn.warps, xt);
+        if (!sh.ok) return cudaErrorInvalidValue;
+        K = sh.K > K ? sh.K : K;
+        smem = sh.smem > smem ? sh.smem : smem;
+    }
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (smem + sizeof(TileMeta) > (size_t)optin) return cudaErrorInvalidValue;
+    std::vector<BatchItem> items;
+    std::vector<int> ntiles;
+    const int nitems = batch_items(g, n, tn.dw, items, ntiles);
+    bl->kind = a0.kind;
+    bl->fdt = a0.fdt;
+    bl->cdt = a0.cdt;
+    bl->K = K;
+    bl->nf = tn.nf;
+    bl->threads = tn.warps * 32;
+    bl->smem = smem;
+    bl->ngrids = n;
+    bl->nitems = nitems;
+    // workspace layout
+    size_t off = 0;
+    bl->off_grids = off;
+    off += align256(gridargs_size(a0.fdt, a0.cdt) * n);
+    bl->off_items = off;
+    off += align256(sizeof(BatchItem) * (size_t)nitems);
+    bl->off_ntiles = off;
+    off += align256(sizeof(int) * (size_t)n);
+    bl->off_parity = off;
+    off += align256(sizeof(int) * (size_t)n);
+    bl->off_counters = off;  // head, status, gdone[n], done[nitems + 1] (the extra flag is never set)
+    bl->counter_bytes = sizeof(int) * (size_t)(2 + n + nitems + 1);
+    off += align256(bl->counter_bytes);
+    bl->bytes = off;
+    bl->items = items;
+    bl->ntiles = ntiles;
+    return cudaSuccess;
+}
+
+template <typename TF, typename TC>
+static cudaError_t batch_upload_t(const BatchGrid* g, int n, const BlockedTune& tn, BatchLaunch* bl, char* ws,
+                                  cudaStream_t s) {
+    std::vector<GridArgs<TF, TC>> ga(n);
+    std::vector<int> par(n);
+    for (int q = 0; q < n; ++q) {
+        const int V = 16 / sizeof(TF);
+        const int xt = ((g[q].a.L.nx + V - 1) / V) * V;
+        BlockedTune t = tn;
+        t.xtile = xt;
+        BlkShape sh = blk_shape_x(g[q].a.kind, g[q].a.fdt, g[q].a.L.nx, tn.dw, tn.nf, tn.warps, xt);
+        ga[q] = grid_args<TF, TC>(g[q].a, g[q].field, g[q].parity, g[q].T, t, sh);
+        par[q] = g[q].parity;
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(ws + bl->off_grids, ga.data(), sizeof(GridArgs<TF, TC>) * n, cudaMemcpyHostToDevice, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(ws + bl->off_items, bl->items.data(), sizeof(BatchItem) * bl->items.size(),
+                             cudaMemcpyHostToDevice, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(ws + bl->off_ntiles, bl->ntiles.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(ws + bl->off_parity, par.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s))) return e;
+    return cudaStreamSynchronize(s);  // host vectors are freed on return
+}
+
+cudaError_t batch_upload(const BatchGrid* g, int n, const BlockedTune& tn, BatchLaunch* bl, void* ws,
+                         cudaStream_t s) {
+    char* w = static_cast<char*>(ws);
+    bl->ws = w;
+    if (bl->fdt == DT_F64) return batch_upload_t<double, double>(g, n, tn, bl, w, s);
+    if (bl->cdt == DT_BF16) return batch_upload_t<float, __nv_bfloat16>(g, n, tn, bl, w, s);
+    return batch_upload_t<float, float>(g, n, tn, bl, w, s);
+}
+
+cudaError_t batch_reupload_items(BatchLaunch* bl, cudaStream_t s) {
+    cudaError_t e = cudaMemcpyAsync(bl->ws + bl->off_items, bl->items.data(), sizeof(BatchItem) * bl->items.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e) return e;
+    return cudaStreamSynchronize(s);
+}
+
+template <int KIND, typename TF, typename TC, int K, int NF>
+static cudaError_t batch_launch_k(const BatchLaunch& bl, cudaStream_t s) {
+    auto kfn = blocked_batch_kernel<KIND, TF, TC, K, NF>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem);
+    if (e) return e;
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, bl.threads, bl.smem);
+    if (e) return e;
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    long long ctas = (long long)per * sms;
+    if (ctas > bl.nitems) ctas = bl.nitems;
+    if (ctas < 1) return cudaSuccess;
+    BatchArgs<TF, TC> A{};
+    char* ws = bl.ws;
+    int* cnt = reinterpret_cast<int*>(ws + bl.off_counters);
+    A.grids = reinterpret_cast<const GridArgs<TF, TC>*>(ws + bl.off_grids);
+    A.items = reinterpret_cast<const BatchItem*>(ws + bl.off_items);
+    A.nitems = bl.nitems;
+    A.head = cnt;
+    A.status = cnt + 1;
+    A.gdone = cnt + 2;
+    A.done = cnt + 2 + bl.ngrids;
+    A.ntiles = reinterpret_cast<const int*>(ws + bl.off_ntiles);
+    A.parity = reinterpret_cast<int*>(ws + bl.off_parity);
+    A.spin_limit = bl.spin_limit;
+    if ((e = cudaMemsetAsync(cnt, 0, bl.counter_bytes, s))) return e;
+    kfn<<<(unsigned)ctas, bl.threads, bl.smem, s>>>(A);
+    return cudaGetLastError();
+}
+
+template <int KIND, typename TF, typename TC>
+static cudaError_t batch_launch_t(const BatchLaunch& bl, cudaStream_t s) {
+#define STG_BAT(KK, NFF) \
+    if (bl.K == KK && bl.nf == NFF) return batch_launch_k<KIND, TF, TC, KK, NFF>(bl, s);
+    STG_BAT(1, 1) STG_BAT(2, 1) STG_BAT(4, 1) STG_BAT(1, 2) STG_BAT(2, 2) STG_BAT(4, 2)
+#undef STG_BAT
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t batch_launch(const BatchLaunch& bl, cudaStream_t s) {
+    switch (bl.kind) {
+        case K7C:
+            if (bl.fdt == DT_F32) return batch_launch_t<K7C, float, float>(bl, s);
+            if (bl.fdt == DT_F64) return batch_launch_t<K7C, double, double>(bl, s);
+            break;
+        case K7V:
+            if (bl.fdt == DT_F32 && bl.cdt == DT_F32) return batch_launch_t<K7V, float, float>(bl, s);
+            if (bl.fdt == DT_F32 && bl.cdt == DT_BF16) return batch_launch_t<K7V, float, __nv_bfloat16>(bl, s);
+            if (bl.fdt == DT_F64) return batch_launch_t<K7V, double, double>(bl, s);
+            break;
+        case K25V:
+            if (bl.fdt == DT_F32 && bl.cdt == DT_F32) return batch_launch_t<K25V, float, float>(bl, s);
+            if (bl.fdt == DT_F32 && bl.cdt == DT_BF16) return batch_launch_t<K25V, float, __nv_bfloat16>(bl, s);
+            if (bl.fdt == DT_F64) return batch_launch_t<K25V, double, double>(bl, s);
             break;
     }
     return cudaErrorInvalidValue;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace stg {
@@ -53,5 +55,33 @@ cudaError_t copy_interior_zero_halo(const Layout& L, int dt, const void* src, vo
 
 // Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);
+
+// ---- persistent batch of grids (blocked schedule, one launch)
+struct BatchItem {
+    int g, k, b;   // grid, diamond row, diamond
+    int dep[3];    // items this one waits for (-1: none)
+};
+
+struct BatchGrid {
+    SweepArgs a;
+    void* field[2];
+    int parity;  // array holding the grid's current time level
+    int T;       // steps to advance
+};
+
+struct BatchLaunch {
+    int kind, fdt, cdt, K, nf, threads, ngrids, nitems;
+    size_t smem, bytes, counter_bytes;
+    size_t off_grids, off_items, off_ntiles, off_parity, off_counters;
+    unsigned spin_limit = 1u << 24;
+    char* ws = nullptr;
+    std::vector<BatchItem> items;
+    std::vector<int> ntiles;
+};
+
+cudaError_t batch_plan(const BatchGrid* g, int n, const BlockedTune& tn, BatchLaunch* bl);
+cudaError_t batch_upload(const BatchGrid* g, int n, const BlockedTune& tn, BatchLaunch* bl, void* ws, cudaStream_t s);
+cudaError_t batch_reupload_items(BatchLaunch* bl, cudaStream_t s);
+cudaError_t batch_launch(const BatchLaunch& bl, cudaStream_t s);
 
 }  // namespace stg

@@ -1,0 +1,97 @@
+"""Persistent batched launch of many grids: bitwise equal to per-grid sweeps,
+CUDA-graph capture and replay, bounded dependency waits."""
+import numpy as np
+import pytest
+
+from paper_1410_5561_gb300 import inputs
+from tests._util import Problem
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [((37, 29, 21), 9), ((16, 45, 12), 13), ((64, 8, 30), 4), ((5, 5, 5), 7), ((50, 33, 17), 1),
+          ((21, 40, 26), 16)]
+
+
+def _problems(kind="7pt_var", fdt="f32", cdt=None, shapes=SHAPES, seed=40):
+    return [(Problem(kind, *sh, fdt=fdt, cdt=cdt, seed=seed + q, halo=0.1 * (q % 3)), T)
+            for q, (sh, T) in enumerate(shapes)]
+
+
+def _plain_result(p, T):
+    s = p.make()
+    s.set_tuning("plain")
+    s.run(T)
+    return s.get_field().cpu().numpy()
+
+
+@pytest.mark.parametrize("kind,fdt,cdt,tn", [
+    ("7pt_var", "f32", None, (8, 1, 16)),
+    ("7pt_var", "f32", "bf16", (6, 2, 8)),
+    ("7pt_const", "f32", None, (8, 2, 16)),
+    ("7pt_const", "f64", None, (4, 1, 8)),
+    ("25pt_var", "f32", None, (8, 1, 8)),
+])
+def test_batch_bitwise_equals_plain(kind, fdt, cdt, tn):
+    from paper_1410_5561_gb300.batch import Batch
+    from paper_1410_5561_gb300.stencil import Tuning
+    probs = _problems(kind, fdt, cdt)
+    grids = [p.make() for p, _ in probs]
+    b = Batch(grids, [T for _, T in probs], Tuning(tn[0], tn[1], tn[2], 0))
+    b.launch()
+    assert b.status() == 0
+    for (p, T), g in zip(probs, grids):
+        assert np.array_equal(g.get_field().cpu().numpy(), _plain_result(p, T))
+
+
+def test_batch_graph_replay():
+    import torch
+    from paper_1410_5561_gb300.batch import Batch
+    from paper_1410_5561_gb300.stencil import Tuning
+    probs = _problems()
+    grids = [p.make() for p, _ in probs]
+    b = Batch(grids, [T for _, T in probs], Tuning(8, 1, 16, 0))
+    b.launch()            # ordinary launch first (one advance)
+    torch.cuda.synchronize()
+    graph = b.capture()   # not executed
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    b.sync_parity()
+    assert b.status() == 0
+    for (p, T), g in zip(probs, grids):
+        assert np.array_equal(g.get_field().cpu().numpy(), _plain_result(p, 3 * T))
+
+
+def test_batch_timeout_is_reported_not_hung():
+    import torch
+    from paper_1410_5561_gb300.batch import Batch
+    from paper_1410_5561_gb300.stencil import Tuning
+    probs = _problems()
+    grids = [p.make() for p, _ in probs]
+    b = Batch(grids, [T for _, T in probs], Tuning(8, 1, 16, 0))
+    b.set_wait_limit(2000)
+    b.inject_stall(b.items // 2)
+    b.launch()
+    torch.cuda.synchronize()
+    from paper_1410_5561_gb300._lib import STATUS
+    assert STATUS[b.status()] == "STENCIL_ETIMEOUT"
+
+
+def test_batch_full_workload_sampled():
+    """The 64-grid batch (sides 32..192, T 10..200, 7-point variable FP32): a graph replay,
+    then a sample of grids checked bitwise against their own plain sweeps."""
+    import torch
+    from paper_1410_5561_gb300.batch import Batch
+    from paper_1410_5561_gb300.stencil import Tuning
+    shapes = inputs.batch_shapes(0)
+    probs = [(Problem("7pt_var", nx, ny, nz, fdt="f32", seed=q), T) for q, (nx, ny, nz, T) in enumerate(shapes)]
+    grids = [p.make() for p, _ in probs]
+    b = Batch(grids, [T for _, T in probs], Tuning(8, 1, 16, 0))
+    graph = b.capture()
+    graph.replay()
+    torch.cuda.synchronize()
+    b.sync_parity()
+    assert b.status() == 0
+    for q in (0, 7, 21, 42, 63):
+        p, T = probs[q]
+        assert np.array_equal(grids[q].get_field().cpu().numpy(), _plain_result(p, T)), q

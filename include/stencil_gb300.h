@@ -233,6 +233,31 @@ int stencil_batch_inject_stall(stencil_batch_t b, int item);
 
 int stencil_batch_destroy(stencil_batch_t b);
 
+/* Run a batch once without any device allocation by the caller or the library.
+ * The paper has no counterpart: this serves callers that cannot allocate device
+ * memory for a workspace, for example code whose device memory is all owned by
+ * another allocator (a framework's caching allocator, a pre-sized arena), or a
+ * latency-critical loop that must not call cudaMalloc because it can
+ * synchronise the device.
+ * Same meaning as stencil_batch_create + stencil_batch_bind + stencil_batch_launch
+ * with the same arguments (grids, T, n, tuning), but the batch's scratch (grid
+ * descriptors, tile list, dependency flags, status) lives in a fixed 4 MiB
+ * array in device memory owned by the library, which every GPU that loads the
+ * library holds until the process exits. A batch whose scratch would exceed
+ * 4 MiB is rejected with STENCIL_EINVAL before anything is launched. The
+ * grids' arrays are the caller's, as usual. The call uploads the plan (waiting
+ * for cuda_stream), enqueues the launch on cuda_stream and updates the grids'
+ * parities; if status_out is not NULL it also waits for the launch and stores
+ * STENCIL_OK or STENCIL_ETIMEOUT there.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the one array and it keeps the last call's
+ * contents; every call rewrites what it needs and resets its counters, but
+ * calls whose work overlaps on the GPU (different streams, or a call enqueued
+ * before the previous one has finished on another stream) race on it. */
+int stencil_batch_run_noalloc(const stencil_t* grids, const int* T, int n, const stencil_tuning* tuning,
+                              void* cuda_stream, int* status_out);
+
 /* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error. */
 int stencil_sync(stencil_t h);
 

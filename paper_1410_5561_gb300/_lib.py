@@ -77,6 +77,8 @@ SIGNATURES = [
     ("stencil_batch_set_wait_limit", _I, [_H, ctypes.c_uint]),
     ("stencil_batch_inject_stall", _I, [_H, _I]),
     ("stencil_batch_destroy", _I, [_H]),
+    ("stencil_batch_run_noalloc", _I, [ctypes.POINTER(_H), ctypes.POINTER(_I), _I, ctypes.POINTER(stencil_tuning),
+                                       _P, ctypes.POINTER(_I)]),
     ("stencil_sync", _I, [_H]),
     ("stencil_strerror", ctypes.c_char_p, [_I]),
     ("stencil_destroy", _I, [_H]),

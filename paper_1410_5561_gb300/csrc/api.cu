@@ -82,6 +82,19 @@ static int check_tune(const stencil_grid* h, const BlockedTune& t) {
     return STENCIL_OK;
 }
 
+namespace stg {
+int grid_batch_view(const stencil_grid* h, SweepArgs* a, void** f0, void** f1, int* parity) {
+    if (!h) return STENCIL_EINVAL;
+    if (!h->bound) return STENCIL_EUNBOUND;
+    *a = args_of(h);
+    *f0 = h->field[0];
+    *f1 = h->field[1];
+    *parity = h->parity;
+    return STENCIL_OK;
+}
+void grid_set_parity(stencil_grid* h, int parity) { h->parity = parity & 1; }
+}  // namespace stg
+
 extern "C" {
 
 int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_dtype, int coef_dtype,

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct stencil_grid;  // the C ABI's grid handle (api.cu)
+
 namespace stg {
 
 enum DType { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
@@ -83,5 +85,10 @@ cudaError_t batch_plan(const BatchGrid* g, int n, const BlockedTune& tn, BatchLa
 cudaError_t batch_upload(const BatchGrid* g, int n, const BlockedTune& tn, BatchLaunch* bl, void* ws, cudaStream_t s);
 cudaError_t batch_reupload_items(BatchLaunch* bl, cudaStream_t s);
 cudaError_t batch_launch(const BatchLaunch& bl, cudaStream_t s);
+
+// Read access to a bound grid handle for batch planning (STENCIL_EUNBOUND if unbound),
+// and the parity update after a batch launch.
+int grid_batch_view(const stencil_grid* h, SweepArgs* a, void** f0, void** f1, int* parity);
+void grid_set_parity(stencil_grid* h, int parity);
 
 }  // namespace stg

@@ -58,8 +58,8 @@ struct TileMeta {
     int ldlo[MAXLV], ldhi[MAXLV];      // ring vectors loaded for this level's input
     short tl[MAXTASK], ty[MAXTASK];    // load / fill tasks for interior planes
     unsigned char tfill[MAXTASK];
-    short il[MAXITEM], iy[MAXITEM];    // compute items (level, row, 32-vector chunk)
-    unsigned char ich[MAXITEM];
+    short il[MAXITEM], iy[MAXITEM];    // compute items (level, first row, 32-vector chunk, rows)
+    unsigned char ich[MAXITEM], inr[MAXITEM];
 };
 
 // Per-grid constants of a blocked sweep.
@@ -122,18 +122,21 @@ __device__ __forceinline__ int fdiv(int a, int b) { return a >= 0 ? a / b : -((-
 __device__ __forceinline__ int cdiv(int a, int b) { return -fdiv(-a, b); }
 __device__ __forceinline__ int wrap_inc(int s, int q) { return s + 1 == q ? 0 : s + 1; }
 
-// Per-warp state of one owned item (level l, row y): pointers and lane flags.
-template <typename TF, int V>
+// Per-warp state of one owned item (level l, RB adjacent rows y0.., one 32-vector
+// chunk): pointers and lane flags.
+template <typename TF, int V, int RB>
 struct Item {
-    const TF* rowp;   // ring row y of level l, slot 0, this lane's vector
-    TF* dstp;         // ring row y of level l+1, slot 0, this lane's vector (or null)
-    TF* gdst;         // HBM array receiving u_{t+1}
-    size_t g0;        // element index of (xg, y, z = 0)
-    int PS, dPS;      // ring plane strides (elements)
-    int zb0;          // z of the item's first plane at step 0 (= -l d)
-    int qr;           // vectors available to the right of this lane's vector
-    int xg;           // interior x of the lane's element 0
-    bool valid, active, indom, full, store;
+    const TF* rowp;    // ring row y0 of level l, slot 0, this lane's vector
+    TF* dstp[RB];      // ring row y0+i of level l+1, slot 0, this lane's vector (or null)
+    TF* gdst;          // HBM array receiving u_{t+1}
+    size_t g0[RB];     // element index of (xg, y0+i, z = 0)
+    int PS, dPS;       // ring plane strides (elements)
+    int zb0;           // z of the item's first plane at step 0 (= -l d)
+    int qr;            // vectors available to the right of this lane's vector
+    int xg;            // interior x of the lane's element 0
+    int nr;            // valid rows (1..RB)
+    bool valid, active, indom, full;
+    bool store[RB];
 };
 
 // One tile (row k, diamond b) of one grid, x tile xti, all z; the whole CTA
@@ -148,6 +151,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     constexpr int J = (R + V - 1) / V;
     constexpr int HV = J * V;
     constexpr bool PERSIST = (R == 1);  // keep z-windows in registers across steps
+    constexpr int RB = PERSIST ? 2 : 1;   // adjacent rows per item (diamond widths are multiples of 2R)
+    static_assert(RB == 1 || R == 1, "two-row items assume radius 1");
     constexpr int WIN = 2 * R + NF;
     using VT = Vec<TF, V>;
 
@@ -218,11 +223,12 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     ++ntask;
                 }
                 const int nch = (cdiv(xh - x0 + EH, V) - M.vlo[l] + 31) / 32;
-                for (int y = lo; y < hi; ++y)
+                for (int y = lo; y < hi; y += RB)
                     for (int c = 0; c < nch && nitem < MAXITEM; ++c) {
                         M.il[nitem] = (short)l;
                         M.iy[nitem] = (short)y;
                         M.ich[nitem] = (unsigned char)c;
+                        M.inr[nitem] = (unsigned char)(hi - y < RB ? hi - y : RB);
                         ++nitem;
                     }
             }
@@ -252,33 +258,39 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     const size_t gplane = L.plane();
 
     // ---- per-warp owned items
-    Item<TF, V> it[K];
-    VT win[K][WIN];
+    Item<TF, V, RB> it[K];
+    VT win[K][RB][WIN];
 #pragma unroll
     for (int kk = 0; kk < K; ++kk) {
-        Item<TF, V>& I = it[kk];
+        Item<TF, V, RB>& I = it[kk];
         const int id = warp + kk * NW;
         I.valid = id < M.nitem;
         if (!I.valid) continue;
-        const int l = M.il[id], y = M.iy[id];
+        const int l = M.il[id], y0 = M.iy[id];
+        I.nr = M.inr[id];
         const int nlo = M.nlo[l];
         I.PS = (M.nhi[l] - nlo) * Xs;
         const int v = M.vlo[l] + 32 * M.ich[id] + lane;
         const int vr = v < nvs ? v : nvs - 1;  // clamped read vector (inactive lanes only)
         I.qr = nvs - 1 - vr;
-        I.rowp = ring + M.roff[l] + (y - nlo) * Xs + vr * V;
+        I.rowp = ring + M.roff[l] + (y0 - nlo) * Xs + vr * V;
         I.xg = x0 - EH + v * V;
         I.active = (I.xg + V > M.xlo[l]) && (I.xg < M.xhi[l]);
         I.indom = I.xg >= 0 && I.xg < Nx;
         I.full = I.xg >= 0 && I.xg + V <= Nx;
-        I.dstp = nullptr;
         I.dPS = 0;
-        if (l + 1 < Lt && y >= M.nlo[l + 1] && y < M.nhi[l + 1]) {
-            I.dstp = ring + M.roff[l + 1] + (y - M.nlo[l + 1]) * Xs + v * V;
-            I.dPS = (M.nhi[l + 1] - M.nlo[l + 1]) * Xs;
+        const bool nxt = l + 1 < Lt;
+        if (nxt) I.dPS = (M.nhi[l + 1] - M.nlo[l + 1]) * Xs;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) {
+            const int y = y0 + (i < I.nr ? i : I.nr - 1);
+            I.dstp[i] = nullptr;
+            if (nxt && y >= M.nlo[l + 1] && y < M.nhi[l + 1])
+                I.dstp[i] = ring + M.roff[l + 1] + (y - M.nlo[l + 1]) * Xs + v * V;
+            I.store[i] = i < I.nr && I.active && I.indom && !(y >= M.wlo[l] && y < M.whi[l]) && I.xg >= x0 &&
+                         I.xg < x0 + Xt;
+            I.g0[i] = I.indom ? L.at(I.xg, y, 0) : 0;
         }
-        I.store = I.active && I.indom && !(y >= M.wlo[l] && y < M.whi[l]) && I.xg >= x0 && I.xg < x0 + Xt;
-        I.g0 = I.indom ? L.at(I.xg, y, 0) : 0;
         I.gdst = P.f[(p0 + M.t0 + l + 1) & 1];
         I.zb0 = -l * d;
     }
@@ -287,9 +299,11 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
 #pragma unroll
         for (int kk = 0; kk < K; ++kk)
 #pragma unroll
-            for (int r = 0; r < WIN; ++r)
+            for (int i = 0; i < RB; ++i)
 #pragma unroll
-                for (int e = 0; e < V; ++e) win[kk][r].v[e] = hv;
+                for (int r = 0; r < WIN; ++r)
+#pragma unroll
+                    for (int e = 0; e < V; ++e) win[kk][i][r].v[e] = hv;
     }
 
     // ---- producer: HBM loads (cp.async) and Dirichlet fills of planes P_l(s) = [s NF - l d + NF + R, +NF)
@@ -354,49 +368,62 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         if (lock) cluster_wait();
 #pragma unroll
         for (int kk = 0; kk < K; ++kk) {
-            Item<TF, V>& I = it[kk];
+            Item<TF, V, RB>& I = it[kk];
             if (!I.valid) continue;
             const int zb = s * NF + I.zb0;
-            int zfirst, zlast, sl = 0, sc = 0;
             if constexpr (PERSIST) {
-                // the window advances every step from the start; planes below 0 are the
+                // the windows advance every step from the start; planes below 0 are the
                 // Dirichlet value, so the ring is never read below the current plane
                 if (zb + NF + R <= 0 || zb >= Nz) continue;  // warp-uniform
-                zfirst = zb;
-                zlast = zb + NF;
             } else {
-                zfirst = zb < 0 ? 0 : zb;
-                zlast = zb + NF < Nz ? zb + NF : Nz;
-                if (zfirst >= zlast) continue;  // warp-uniform
-                sl = pmod(zfirst - R, Q);       // slot of plane zfirst - R
-#pragma unroll
-                for (int r = 0; r < 2 * R; ++r) {
-                    win[kk][r] = ldv<TF, V>(I.rowp + sl * I.PS);
-                    sl = wrap_inc(sl, Q);
-                }
-                sc = sl - R < 0 ? sl - R + Q : sl - R;  // slot of plane zfirst
+                if (zb + NF <= 0 || zb >= Nz) continue;  // warp-uniform
             }
+            const int s0 = pmod(zb, Q);  // ring slot of plane zb
 #pragma unroll
             for (int f = 0; f < NF; ++f) {
-                const int z = zfirst + f;
-                bool live;
+                const int z = zb + f;
+                int sc = s0 + f;
+                if (sc >= Q) sc -= Q;  // slot of plane z
                 if constexpr (PERSIST) {
-                    const int pz = z + R;  // newest plane of the window
-                    if (pz >= 0 && z < Nz) {
-                        win[kk][2 * R + f] = ldv<TF, V>(I.rowp + (pz % Q) * I.PS);
-                    } else {
+                    int sn = sc + R;
+                    if (sn >= Q) sn -= Q;  // slot of plane z + R
+                    const bool loadnew = z + R >= 0 && z < Nz;
 #pragma unroll
-                        for (int e = 0; e < V; ++e) win[kk][2 * R + f].v[e] = hv;
+                    for (int i = 0; i < RB; ++i) {
+                        if (loadnew) {
+                            const int ri = i < I.nr ? i : I.nr - 1;
+                            win[kk][i][2 * R + f] = ldv<TF, V>(I.rowp + ri * Xs + sn * I.PS);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < V; ++e) win[kk][i][2 * R + f].v[e] = hv;
+                        }
                     }
-                    live = z >= 0 && z < Nz;
-                    sc = live ? z % Q : 0;
                 } else {
-                    live = z < zlast;
-                    if (live) win[kk][2 * R + f] = ldv<TF, V>(I.rowp + sl * I.PS);  // plane z + R
+                    if (z >= 0 && z < Nz) {
+                        // reload the window of planes z - R .. z + R from the ring
+                        int sw = sc - R;
+                        if (sw < 0) sw += Q;
+#pragma unroll
+                        for (int r = 0; r < 2 * R + 1; ++r) {
+                            win[kk][0][f + r] = ldv<TF, V>(I.rowp + sw * I.PS);
+                            sw = wrap_inc(sw, Q);
+                        }
+                    }
                 }
-                if (live) {
-                    const VT& ctr = win[kk][f + R];
-                    const TF* cp = I.rowp + sc * I.PS;
+                if (z < 0 || z >= Nz) continue;
+                const TF* cpb = I.rowp + sc * I.PS;  // row y0 at plane z
+                VT ydn[R], yup[R];                   // rows y0 - r and y0 + nr - 1 + r
+#pragma unroll
+                for (int r = 1; r <= R; ++r) {
+                    ydn[r - 1] = ldv<TF, V>(cpb - r * Xs);
+                    yup[r - 1] = ldv<TF, V>(cpb + (I.nr - 1 + r) * Xs);
+                }
+                const size_t zoff = (size_t)z * gplane;
+#pragma unroll
+                for (int i = 0; i < RB; ++i) {
+                    if (i >= I.nr) continue;  // warp-uniform
+                    const VT& ctr = win[kk][i][f + R];
+                    const TF* cp = cpb + i * Xs;
                     TF xl[(2 * J + 1) * V];
 #pragma unroll
                     for (int e = 0; e < V; ++e) xl[J * V + e] = ctr.v[e];
@@ -417,13 +444,19 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                             }
                         }
                     }
+                    // y neighbours: other rows of this item from the windows, the rest loaded
                     VT ypv[R], ymv[R];
 #pragma unroll
                     for (int r = 1; r <= R; ++r) {
-                        ypv[r - 1] = ldv<TF, V>(cp + r * Xs);
-                        ymv[r - 1] = ldv<TF, V>(cp - r * Xs);
+                        if constexpr (RB == 1) {
+                            ymv[r - 1] = ydn[r - 1];
+                            ypv[r - 1] = yup[r - 1];
+                        } else {  // two rows, R = 1
+                            ymv[0] = i == 0 ? ydn[0] : win[kk][0][f + R];
+                            ypv[0] = (i == 0 && I.nr == 2) ? win[kk][RB - 1][f + R] : yup[0];
+                        }
                     }
-                    const size_t gidx = I.g0 + (size_t)z * gplane;
+                    const size_t gidx = I.g0[i] + zoff;
                     Vec<TC, V> cv[NC > 0 ? NC : 1];
                     if constexpr (NC > 0) {
                         if (I.active && I.indom) {
@@ -440,8 +473,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
 #pragma unroll
                     for (int e = 0; e < V; ++e) {
                         const int xc = J * V + e;
-                        const VT& zp1 = win[kk][f + R + 1];
-                        const VT& zm1 = win[kk][f + R - 1];
+                        const VT& zp1 = win[kk][i][f + R + 1];
+                        const VT& zm1 = win[kk][i][f + R - 1];
                         if constexpr (KIND == K7C) {
                             out.v[e] = upd7c<TF>(P.c0, P.c1, ctr.v[e], xl[xc + 1], xl[xc - 1], ypv[0].v[e],
                                                  ymv[0].v[e], zp1.v[e], zm1.v[e]);
@@ -461,8 +494,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                                 xm[q] = xl[xc - q - 1];
                                 yp4[q] = ypv[q].v[e];
                                 ym4[q] = ymv[q].v[e];
-                                zp[q] = win[kk][f + R + q + 1].v[e];
-                                zm[q] = win[kk][f + R - q - 1].v[e];
+                                zp[q] = win[kk][i][f + R + q + 1].v[e];
+                                zm[q] = win[kk][i][f + R - q - 1].v[e];
                             }
                             out.v[e] = upd25v<TF>(c, ctr.v[e], xp, xm, yp4, ym4, zp, zm);
                         }
@@ -472,8 +505,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                         for (int e = 0; e < V; ++e)
                             if (!(I.xg + e >= 0 && I.xg + e < Nx)) out.v[e] = hv;
                     }
-                    if (I.active && I.dstp) stv<TF, V>(I.dstp + sc * I.dPS, out);
-                    if (I.store) {
+                    if (I.active && I.dstp[i]) stv<TF, V>(I.dstp[i] + sc * I.dPS, out);
+                    if (I.store[i]) {
                         if (I.full) {
                             stv<TF, V>(I.gdst + gidx, out);
                         } else {
@@ -482,17 +515,14 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                                 if (I.xg + e < Nx) I.gdst[gidx + e] = out.v[e];
                         }
                     }
-                    if constexpr (!PERSIST) {
-                        sl = wrap_inc(sl, Q);
-                        sc = wrap_inc(sc, Q);
-                    }
                 }
             }
             if constexpr (PERSIST) {
 #pragma unroll
-                for (int r = 0; r < 2 * R; ++r) win[kk][r] = win[kk][r + NF];
+                for (int i = 0; i < RB; ++i)
+#pragma unroll
+                    for (int r = 0; r < 2 * R; ++r) win[kk][i][r] = win[kk][i][r + NF];
             }
-            (void)zlast;
         }
         cp_async_wait_1();
         __syncthreads();
@@ -634,7 +664,10 @@ static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps
     if ((nx + xtile - 1) / xtile > MAXCLUSTER) return s;
     int ov = ltmax > 1 ? (R * (ltmax - 1) + s.V - 1) / s.V : 0;
     s.nch = (xtile / s.V + 2 * ov + 31) / 32;
-    int items = item_bound(dw, R) * s.nch;
+    // rows per item, as in the kernel; unclipped widths are multiples of 2R, and clipping
+    // only removes rows, so ceil(w / rb) summed over the levels never exceeds D^2/(2R rb)
+    const int rb = R == 1 ? 2 : 1;
+    int items = item_bound(dw, R) / rb * s.nch;
     if (items > MAXITEM) return s;
     int K = (items + warps - 1) / warps;
     if (K > 4) return s;

@@ -106,6 +106,6 @@ def test_infeasible_tuning_rejected():
     with pytest.raises(StencilError):
         s.set_tuning("blocked", Tuning(8, 3, 8, 64))   # more than two frontlines
     with pytest.raises(StencilError):
-        s.set_tuning("blocked", Tuning(16, 1, 16, 64))  # 128 rows exceed 16 warps x 4 rows
+        s.set_tuning("blocked", Tuning(24, 1, 8, 64))   # 288 rows exceed 8 warps x 4 two-row items
     with pytest.raises(StencilError):
         s.set_tuning("blocked", Tuning(8, 1, 8, 2))    # x tile narrower than one vector

@@ -101,6 +101,9 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16_u32(uint32_t s, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
@@ -113,6 +116,32 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
+
+// Shared-memory vector access through 32-bit shared-window addresses.
+template <typename TF, int V> struct Lds;
+template <> struct Lds<float, 4> {
+    static __device__ __forceinline__ Vec<float, 4> ld(uint32_t a) {
+        Vec<float, 4> r;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                     : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, const Vec<float, 4>& x) {
+        asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};\n" ::"r"(a), "f"(x.v[0]), "f"(x.v[1]), "f"(x.v[2]),
+                     "f"(x.v[3]));
+    }
+};
+template <> struct Lds<double, 2> {
+    static __device__ __forceinline__ Vec<double, 2> ld(uint32_t a) {
+        Vec<double, 2> r;
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(r.v[0]), "=d"(r.v[1]) : "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, const Vec<double, 2>& x) {
+        asm volatile("st.shared.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(x.v[0]), "d"(x.v[1]));
+    }
+};
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ int pmod(int a, int q) {
     int r = a % q;
@@ -135,6 +164,8 @@ struct Item {
     int qr;            // vectors available to the right of this lane's vector
     int xg;            // interior x of the lane's element 0
     int nr;            // valid rows (1..RB)
+    uint32_t ar;       // shared address of rowp
+    uint32_t ad[RB];   // shared address of dstp[i] (unused when dstp[i] is null)
     bool valid, active, indom, full;
     bool store[RB];
 };
@@ -293,6 +324,9 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         }
         I.gdst = P.f[(p0 + M.t0 + l + 1) & 1];
         I.zb0 = -l * d;
+        I.ar = smem_u32(I.rowp);
+#pragma unroll
+        for (int i = 0; i < RB; ++i) I.ad[i] = I.dstp[i] ? smem_u32(I.dstp[i]) : 0u;
     }
 
     if constexpr (PERSIST) {
@@ -307,11 +341,57 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     }
 
     // ---- producer: HBM loads (cp.async) and Dirichlet fills of planes P_l(s) = [s NF - l d + NF + R, +NF)
+    // Load / fill tasks owned by this warp (tasks warp, warp + NW, ...): the first KT
+    // are kept in registers for the whole sweep, any further ones are re-derived each step.
+    constexpr int KT = 2;
+    uint32_t ta_ring[KT];  // shared address: task row, slot 0, this lane's first vector
+    uint32_t ta_psb[KT];   // plane stride of the task's ring (bytes)
+    const TF* ta_src[KT];  // this lane's first vector of the task row at z = 0 (null: fill)
+    int ta_zb0[KT];        // first plane at step 0
+    int ta_nv[KT];         // vectors this lane moves per plane
+#pragma unroll
+    for (int j = 0; j < KT; ++j) {
+        const int ti = warp + j * NW;
+        ta_nv[j] = 0;
+        ta_zb0[j] = 0;
+        ta_ring[j] = 0;
+        ta_psb[j] = 0;
+        ta_src[j] = nullptr;
+        if (ti >= ntask) continue;
+        const int l = M.tl[ti], y = M.ty[ti];
+        const int nlo = M.nlo[l];
+        const int ldlo = M.ldlo[l], ldhi = M.ldhi[l];
+        const int c0 = ldlo + lane;
+        ta_nv[j] = c0 < ldhi ? (ldhi - c0 + 31) / 32 : 0;
+        ta_psb[j] = (uint32_t)((M.nhi[l] - nlo) * Xs * (int)sizeof(TF));
+        ta_ring[j] = smem_u32(ring + M.roff[l] + (y - nlo) * Xs + c0 * V);
+        ta_zb0[j] = -l * d + NF + R;
+        if (!M.tfill[ti])
+            ta_src[j] = P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH) + (ptrdiff_t)c0 * V;
+    }
+
     auto produce = [&](int s) {
         VT hvv;
 #pragma unroll
         for (int e = 0; e < V; ++e) hvv.v[e] = hv;
-        for (int ti = warp; ti < ntask; ti += NW) {
+#pragma unroll
+        for (int j = 0; j < KT; ++j) {
+            if (ta_nv[j] == 0 && warp + j * NW >= ntask) continue;
+#pragma unroll
+            for (int fz = 0; fz < NF; ++fz) {
+                const int z = s * NF + ta_zb0[j] + fz;
+                if (z < 0 || z >= Nz) continue;
+                const uint32_t dst = ta_ring[j] + (uint32_t)pmod(z, Q) * ta_psb[j];
+                if (ta_src[j] == nullptr) {
+                    for (int c = 0; c < ta_nv[j]; ++c) Lds<TF, V>::st(dst + (uint32_t)(c * 32 * V * (int)sizeof(TF)), hvv);
+                } else {
+                    const TF* gp = ta_src[j] + (size_t)z * gplane;
+                    for (int c = 0; c < ta_nv[j]; ++c)
+                        cp_async16_u32(dst + (uint32_t)(c * 32 * V * (int)sizeof(TF)), gp + c * 32 * V);
+                }
+            }
+        }
+        for (int ti = warp + KT * NW; ti < ntask; ti += NW) {
             const int l = M.tl[ti], y = M.ty[ti];
             const bool fill = M.tfill[ti] != 0;
             const int nlo = M.nlo[l];
@@ -388,11 +468,12 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     int sn = sc + R;
                     if (sn >= Q) sn -= Q;  // slot of plane z + R
                     const bool loadnew = z + R >= 0 && z < Nz;
+                    const uint32_t an = I.ar + (uint32_t)(sn * I.PS * (int)sizeof(TF));
 #pragma unroll
                     for (int i = 0; i < RB; ++i) {
                         if (loadnew) {
                             const int ri = i < I.nr ? i : I.nr - 1;
-                            win[kk][i][2 * R + f] = ldv<TF, V>(I.rowp + ri * Xs + sn * I.PS);
+                            win[kk][i][2 * R + f] = Lds<TF, V>::ld(an + (uint32_t)(ri * Xs * (int)sizeof(TF)));
                         } else {
 #pragma unroll
                             for (int e = 0; e < V; ++e) win[kk][i][2 * R + f].v[e] = hv;
@@ -411,27 +492,28 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     }
                 }
                 if (z < 0 || z >= Nz) continue;
-                const TF* cpb = I.rowp + sc * I.PS;  // row y0 at plane z
+                const uint32_t acb = I.ar + (uint32_t)(sc * I.PS * (int)sizeof(TF));
+                constexpr int XB = (int)sizeof(TF);
                 VT ydn[R], yup[R];                   // rows y0 - r and y0 + nr - 1 + r
 #pragma unroll
                 for (int r = 1; r <= R; ++r) {
-                    ydn[r - 1] = ldv<TF, V>(cpb - r * Xs);
-                    yup[r - 1] = ldv<TF, V>(cpb + (I.nr - 1 + r) * Xs);
+                    ydn[r - 1] = Lds<TF, V>::ld(acb - (uint32_t)(r * Xs * XB));
+                    yup[r - 1] = Lds<TF, V>::ld(acb + (uint32_t)((I.nr - 1 + r) * Xs * XB));
                 }
                 const size_t zoff = (size_t)z * gplane;
 #pragma unroll
                 for (int i = 0; i < RB; ++i) {
                     if (i >= I.nr) continue;  // warp-uniform
                     const VT& ctr = win[kk][i][f + R];
-                    const TF* cp = cpb + i * Xs;
+                    const uint32_t ac = acb + (uint32_t)(i * Xs * XB);
                     TF xl[(2 * J + 1) * V];
 #pragma unroll
                     for (int e = 0; e < V; ++e) xl[J * V + e] = ctr.v[e];
 #pragma unroll
                     for (int q = 1; q <= J; ++q) {
                         VT lf{}, rt{};
-                        if (lane < q) lf = ldv<TF, V>(cp - q * V);
-                        if (lane >= 32 - q) rt = ldv<TF, V>(cp + (q <= I.qr ? q : I.qr) * V);
+                        if (lane < q) lf = Lds<TF, V>::ld(ac - (uint32_t)(q * V * XB));
+                        if (lane >= 32 - q) rt = Lds<TF, V>::ld(ac + (uint32_t)((q <= I.qr ? q : I.qr) * V * XB));
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             if ((J - q) * V + e >= J * V - R) {  // within R to the left
@@ -505,7 +587,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                         for (int e = 0; e < V; ++e)
                             if (!(I.xg + e >= 0 && I.xg + e < Nx)) out.v[e] = hv;
                     }
-                    if (I.active && I.dstp[i]) stv<TF, V>(I.dstp[i] + sc * I.dPS, out);
+                    if (I.active && I.dstp[i]) Lds<TF, V>::st(I.ad[i] + (uint32_t)(sc * I.dPS * XB), out);
                     if (I.store[i]) {
                         if (I.full) {
                             stv<TF, V>(I.gdst + gidx, out);

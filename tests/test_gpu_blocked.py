@@ -102,7 +102,7 @@ def test_infeasible_tuning_rejected():
     with pytest.raises(StencilError):
         s.set_tuning("blocked", Tuning(8, 1, 8, 6))    # x tile not a multiple of 4 floats
     with pytest.raises(StencilError):
-        s.set_tuning("blocked", Tuning(8, 1, 8, 128))  # tile row plus overlap wider than a warp
+        s.set_tuning("blocked", Tuning(8, 1, 8, 4100))  # x tile wider than the 4096-column limit
     with pytest.raises(StencilError):
         s.set_tuning("blocked", Tuning(8, 3, 8, 64))   # more than two frontlines
     with pytest.raises(StencilError):

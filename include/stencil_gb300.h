@@ -99,8 +99,11 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
  * (STENCIL_GRAD_ARRAY, same element index, 8-byte elements) of this grid. */
 int stencil_layout_of(stencil_t h, int which, stencil_layout* out);
 
-/* Bytes of device workspace run() needs (caller-allocated, passed to bind;
- * may be 0). */
+/* Bytes of device workspace the handle can use (caller-allocated, passed to
+ * bind). With a workspace bound, the blocked schedule runs as one persistent
+ * launch whose thread-block clusters walk the dependency-ordered list of
+ * diamond tiles (the plan is kept in the workspace); without one (NULL) it
+ * runs one launch per diamond row. */
 size_t stencil_workspace_bytes(stencil_t h);
 
 /* Bind caller-owned device arrays: field_a, field_b (field layout; ping-pong

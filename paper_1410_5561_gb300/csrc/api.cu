@@ -26,6 +26,7 @@ struct stencil_grid {
     BlockedTune tune;
     bool tune_set;
     long long launches;
+    long long plan_key;  // persistent blocked plan currently in the workspace (-1: none)
 };
 
 static int from_cuda(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
@@ -138,6 +139,7 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
     h->scheme = STENCIL_PLAIN;
     h->tune_set = false;
     h->launches = 0;
+    h->plan_key = -1;
     *out = h;
     return STENCIL_OK;
 }
@@ -160,7 +162,7 @@ int stencil_layout_of(stencil_t h, int which, stencil_layout* out) {
 
 size_t stencil_workspace_bytes(stencil_t h) {
     (void)h;
-    return 0;
+    return GRID_WORKSPACE_BYTES;
 }
 
 int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, void* workspace) {
@@ -173,7 +175,9 @@ int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, v
     h->field[0] = field_a;
     h->field[1] = field_b;
     for (int m = 0; m < 13; ++m) h->coef[m] = m < nc ? coef[m] : nullptr;
+    if (workspace && !aligned16(workspace)) return STENCIL_EINVAL;
     h->ws = workspace;
+    h->plan_key = -1;
     h->bound = true;
     return STENCIL_OK;
 }
@@ -271,7 +275,19 @@ int stencil_run(stencil_t h, int T) {
     if (T == 0) return STENCIL_OK;
     SweepArgs a = args_of(h);
     if (h->scheme == STENCIL_BLOCKED) {
-        cudaError_t e = blocked_run(a, h->field, h->parity, T, h->tune, h->stream, &h->launches);
+        cudaError_t e = cudaErrorNotReady;
+        if (h->ws) {
+            // one persistent launch; if the workspace cannot hold the plan for T steps,
+            // run the steps in two parts
+            e = blocked_run_persistent(a, h->field, h->parity, T, h->tune, h->ws, GRID_WORKSPACE_BYTES, h->stream,
+                                       &h->launches, &h->plan_key);
+            if (e == cudaErrorNotReady && T > 1) {
+                int rc = stencil_run(h, T / 2);
+                if (rc != STENCIL_OK) return rc;
+                return stencil_run(h, T - T / 2);
+            }
+        }
+        if (e == cudaErrorNotReady) e = blocked_run(a, h->field, h->parity, T, h->tune, h->stream, &h->launches);
         if (e == cudaErrorInvalidValue) return STENCIL_EINVAL;
         if (e != cudaSuccess) return STENCIL_ECUDA;
     } else {

@@ -705,6 +705,58 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_batch_kernel(const BatchA
     }
 }
 
+
+// ------------------------------------------------------- persistent single grid
+// The tiles of one grid in row order; cluster c (the x tiles of a diamond, in
+// lockstep) processes tiles c, c + NC, c + 2 NC, ... Every tile waits until the
+// tiles it depends on have been published by all of their x tiles. Clusters
+// are launched only as many as can be resident, and each walks its tiles in
+// increasing order while depending only on smaller indices, so the smallest
+// unfinished tile can always proceed. A wait that exceeds its limit records
+// the status word and proceeds (the results are then invalid but every CTA of
+// the cluster keeps to the same barriers, so nothing can hang).
+template <typename TF, typename TC>
+struct PersistArgs {
+    GridArgs<TF, TC> G;
+    const BatchItem* items;
+    int nitems;
+    int* done;    // per item: x tiles finished
+    int* status;  // 0 ok, 1 a dependency wait gave up
+    unsigned spin_limit;
+};
+
+template <int KIND, typename TF, typename TC, int K, int NF>
+__global__ void __launch_bounds__(BLK_MAXT, 1) blocked_persist_kernel(const PersistArgs<TF, TC> A) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ TileMeta M;
+    TF* ring = reinterpret_cast<TF*>(smem_raw);
+    const int CX = A.G.CX;
+    const int nclusters = (int)gridDim.y;
+    for (int i = (int)blockIdx.y; i < A.nitems; i += nclusters) {
+        const BatchItem it = A.items[i];
+        if (threadIdx.x == 0) {
+            for (int q = 0; q < 3; ++q) {
+                const int dd = it.dep[q];
+                if (dd < 0) continue;
+                unsigned n = 0;
+                while (ld_acquire_gpu(A.done + dd) < CX) {
+                    if (ld_volatile(A.status) != 0) break;
+                    if (++n > A.spin_limit) {
+                        atomicCAS(A.status, 0, 1);
+                        break;
+                    }
+                    __nanosleep(128);
+                }
+            }
+        }
+        __syncthreads();
+        run_tile<KIND, TF, TC, K, NF>(A.G, it.k, it.b, (int)blockIdx.x, CX > 1, A.G.p0, M, ring);
+        __threadfence();  // this thread's HBM stores of the tile are visible GPU-wide
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(A.done + i, 1);
+    }
+}
+
 // ------------------------------------------------------------------- host side
 
 static int ring_rows_bound(int D, int R) {
@@ -1124,6 +1176,122 @@ cudaError_t batch_launch(const BatchLaunch& bl, cudaStream_t s) {
             if (bl.fdt == DT_F32 && bl.cdt == DT_F32) return batch_launch_t<K25V, float, float>(bl, s);
             if (bl.fdt == DT_F32 && bl.cdt == DT_BF16) return batch_launch_t<K25V, float, __nv_bfloat16>(bl, s);
             if (bl.fdt == DT_F64) return batch_launch_t<K25V, double, double>(bl, s);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+
+// Persistent single-grid run: the plan (tile list) lives in the caller's workspace.
+// Returns cudaErrorNotReady when the workspace cannot hold the plan for T steps
+// (the caller then runs T in parts or falls back to row launches).
+template <int KIND, typename TF, typename TC, int K, int NF>
+static cudaError_t persist_k(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
+                             const BlkShape& sh, void* ws, size_t ws_bytes, cudaStream_t st, long long* launches,
+                             long long* plan_key) {
+    BatchGrid g{};
+    g.a = a;
+    g.field[0] = field[0];
+    g.field[1] = field[1];
+    g.parity = p0;
+    g.T = T;
+    std::vector<BatchItem> items;
+    std::vector<int> ntiles;
+    const int n = batch_items(&g, 1, tn.dw, items, ntiles);
+    if (n == 0) return cudaSuccess;
+    const size_t items_bytes = align256(sizeof(BatchItem) * (size_t)n);
+    const size_t need = items_bytes + align256(sizeof(int) * (size_t)(n + 1));
+    if (need > ws_bytes) return cudaErrorNotReady;
+    auto kfn = blocked_persist_kernel<KIND, TF, TC, K, NF>;
+    cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    if (e) return e;
+    const int nxt = (a.L.nx + sh.Xt - 1) / sh.Xt;
+    if (nxt > 8 && (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.blockDim = dim3((unsigned)(tn.warps * 32), 1, 1);
+    cfg.dynamicSmemBytes = sh.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nxt;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)nxt, 1, 1);
+    int nclusters = 0;
+    if (nxt > 1) {
+        e = cudaOccupancyMaxActiveClusters(&nclusters, (void*)kfn, &cfg);
+        if (e) return e;
+    } else {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, tn.warps * 32, sh.smem))) return e;
+        nclusters = per * sms;
+    }
+    if (nclusters < 1) return cudaErrorInvalidConfiguration;
+    if (nclusters > n) nclusters = n;
+    char* w = static_cast<char*>(ws);
+    int* done = reinterpret_cast<int*>(w + items_bytes);
+    // the tile list depends only on (T, D_w, shape): upload it once per change
+    const long long key = ((long long)T << 32) ^ ((long long)tn.dw << 16) ^ (long long)a.L.ny;
+    if (!plan_key || *plan_key != key) {
+        if ((e = cudaMemcpyAsync(w, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st)))
+            return e;
+        if ((e = cudaStreamSynchronize(st))) return e;  // the host copy of the plan goes out of scope
+        if (plan_key) *plan_key = key;
+    }
+    if ((e = cudaMemsetAsync(done, 0, sizeof(int) * (size_t)(n + 1), st))) return e;
+    PersistArgs<TF, TC> A{};
+    A.G = grid_args<TF, TC>(a, field, p0, T, tn, sh);
+    A.G.CX = nxt;
+    A.items = reinterpret_cast<const BatchItem*>(w);
+    A.nitems = n;
+    A.done = done;
+    A.status = done + n;
+    A.spin_limit = 1u << 24;
+    cfg.gridDim = dim3((unsigned)nxt, (unsigned)nclusters, 1);
+    cfg.numAttrs = nxt > 1 ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, kfn, A);
+    if (e) return e;
+    if (launches) *launches += 2;
+    return cudaSuccess;
+}
+
+template <int KIND, typename TF, typename TC>
+static cudaError_t persist_t(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
+                             void* ws, size_t ws_bytes, cudaStream_t st, long long* launches, long long* pk) {
+    BlkShape sh = blk_shape(a, tn);
+    if (!sh.ok) return cudaErrorInvalidValue;
+#define STG_PER(KK, NFF) \
+    if (sh.K == KK && tn.nf == NFF) return persist_k<KIND, TF, TC, KK, NFF>(a, field, p0, T, tn, sh, ws, ws_bytes, st, launches, pk);
+    STG_PER(1, 1) STG_PER(2, 1) STG_PER(4, 1) STG_PER(1, 2) STG_PER(2, 2) STG_PER(4, 2)
+#undef STG_PER
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t blocked_run_persistent(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
+                                   void* ws, size_t ws_bytes, cudaStream_t s, long long* launches, long long* pk) {
+    if (T <= 0 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
+    switch (a.kind) {
+        case K7C:
+            if (a.fdt == DT_F32) return persist_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            if (a.fdt == DT_F64) return persist_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            break;
+        case K7V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32)
+                return persist_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
+                return persist_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            if (a.fdt == DT_F64) return persist_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            break;
+        case K25V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32)
+                return persist_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
+                return persist_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            if (a.fdt == DT_F64) return persist_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
             break;
     }
     return cudaErrorInvalidValue;

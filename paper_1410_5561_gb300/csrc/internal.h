@@ -55,6 +55,15 @@ cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, const void* u, 
 // dst = src on the interior, 0 on every other cell (FP32 / FP64).
 cudaError_t copy_interior_zero_halo(const Layout& L, int dt, const void* src, void* dst, cudaStream_t s);
 
+// Blocked run of T steps by one persistent launch whose clusters walk the
+// dependency-ordered tile list (plan kept in ws). cudaErrorNotReady: ws too small
+// for T. plan_key caches the uploaded plan (reset it when ws changes).
+cudaError_t blocked_run_persistent(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tune,
+                                   void* ws, size_t ws_bytes, cudaStream_t s, long long* launches, long long* plan_key);
+
+// Workspace a grid handle asks for: room for the persistent blocked plan.
+constexpr size_t GRID_WORKSPACE_BYTES = size_t(4) << 20;
+
 // Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);
 

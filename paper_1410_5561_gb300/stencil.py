@@ -57,7 +57,7 @@ class Stencil:
     """One grid: two field arrays (ping-pong), coefficient arrays, workspace."""
 
     def __init__(self, kind, nx: int, ny: int, nz: int, dtype=torch.float32, coef_dtype=None,
-                 device=None, stream: torch.cuda.Stream | None = None):
+                 device=None, stream: torch.cuda.Stream | None = None, workspace: bool = True):
         self.kind = kind_id(kind)
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.dtype = dtype
@@ -78,7 +78,7 @@ class Stencil:
             cl = self._layout(C.STENCIL_COEF_ARRAY)
             self.coefs = [torch.empty(cl.bytes // cl.elem_bytes, dtype=self.coef_dtype, device=self.device)
                           for _ in range(self.ncoef)]
-        wsb = int(C.lib().stencil_workspace_bytes(self._h))
+        wsb = int(C.lib().stencil_workspace_bytes(self._h)) if workspace else 0
         self.workspace = torch.empty(max(wsb, 16), dtype=torch.uint8, device=self.device) if wsb else None
         carr = (ctypes.c_void_p * 13)(*[c.data_ptr() for c in self.coefs])
         C.call("stencil_bind", self._h, _ptr(self.fields[0]), _ptr(self.fields[1]),

@@ -61,12 +61,13 @@ class Problem:
                 coefs = torch.from_numpy(self.coefs).to(device=device, dtype=tdt)
         return u0, coefs
 
-    def make(self, device="cuda"):
+    def make(self, device="cuda", workspace=True):
         import torch
         from paper_1410_5561_gb300.stencil import Stencil
         tdt = {"f32": torch.float32, "f64": torch.float64}[self.fdt]
         cdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[self.cdt]
-        s = Stencil(self.kind, self.nx, self.ny, self.nz, dtype=tdt, coef_dtype=cdt, device=device)
+        s = Stencil(self.kind, self.nx, self.ny, self.nz, dtype=tdt, coef_dtype=cdt, device=device,
+                    workspace=workspace)
         u0, coefs = self.torch_inputs(device)
         if self.kind == "7pt_const":
             s.set_coeffs(scalars=self.scalars)

@@ -16,8 +16,8 @@ from tests._util import Problem, step_tol
 pytestmark = pytest.mark.gpu
 
 
-def _run(p, T, scheme, tuning=None):
-    s = p.make()
+def _run(p, T, scheme, tuning=None, workspace=True):
+    s = p.make(workspace=workspace)
     s.set_tuning(scheme, tuning)
     s.run(T)
     return s.get_field().cpu().numpy()
@@ -109,3 +109,29 @@ def test_infeasible_tuning_rejected():
         s.set_tuning("blocked", Tuning(24, 1, 8, 64))   # 288 rows exceed 8 warps x 4 two-row items
     with pytest.raises(StencilError):
         s.set_tuning("blocked", Tuning(8, 1, 8, 2))    # x tile narrower than one vector
+
+
+@pytest.mark.parametrize("kind,shape,fdt,tn", [
+    ("7pt_const", (45, 37, 23), "f32", Tuning(8, 2, 8, 12)),
+    ("7pt_var", (33, 29, 19), "f32", Tuning(6, 1, 8, 8)),
+    ("25pt_var", (29, 35, 21), "f32", Tuning(16, 1, 8, 12)),
+    ("7pt_const", (30, 21, 12), "f64", Tuning(8, 1, 8, 16)),
+])
+@pytest.mark.parametrize("T", [3, 11])
+def test_row_launches_and_persistent_clusters_agree(kind, shape, fdt, tn, T):
+    """Without a workspace the blocked schedule runs one launch per diamond row; with one
+    it is a single persistent launch over the dependency-ordered tile list."""
+    p = Problem(kind, *shape, fdt=fdt, seed=16, halo=0.2)
+    a = _run(p, T, "blocked", tn, workspace=False)
+    b = _run(p, T, "blocked", tn, workspace=True)
+    c = _run(p, T, "plain")
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_persistent_plan_larger_than_workspace_is_split():
+    """D_w = 2 gives one diamond row per step: 301 rows x 1025 tiles do not fit the
+    4 MiB workspace, so the run is split into parts; the result must not change."""
+    p = Problem("7pt_var", 4, 2048, 4, fdt="f32", seed=17)
+    a = _run(p, 300, "plain")
+    b = _run(p, 300, "blocked", Tuning(2, 1, 4, 4))
+    assert np.array_equal(a, b)

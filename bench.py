@@ -308,7 +308,7 @@ def run_ours(args):
     lups = float(n) ** 3 * T
 
     # autotune the blocked schedule on the real grid, then reset the field
-    tn, table = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+    tn, table = tuner.best_blocked(s, T, reps=1, max_candidates=6)
     s.set_field(u0, halo=0.0)
 
     # headline: blocked
@@ -457,7 +457,7 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
         s.set_tuning("plain")
         tp = timed(s, T, 2, 1) / 2
         try:
-            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=5)
             tb = timed(s, T, 2, 1) / 2
             tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
             bb = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)

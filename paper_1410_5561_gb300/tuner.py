@@ -39,7 +39,10 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
     out = []
     for dw in range(2 * r, max_dw + 1, 2 * r):
         xt = one_warp_xtile(dw, r, v)
-        for xtile in sorted({xt, max(v, (xt // 2) // v * v)}, reverse=True):
+        xts = {xt, max(v, (xt // 2) // v * v)}
+        for nclu in (2, 4, 8):  # x tiles splitting the row into portable cluster sizes
+            xts.add(max(v, ((s.nx + nclu - 1) // nclu + v - 1) // v * v))
+        for xtile in sorted(xts, reverse=True):
             for nf in nfs:
                 for w in warps:
                     t = Tuning(dw, nf, w, xtile)
@@ -49,7 +52,14 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
     kind = _KIND_NAME[s.kind]
     fdt = _DT_NAME[s.dtype]
     cdt = _DT_NAME[s.coef_dtype]
-    out.sort(key=lambda t: (model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw), -t.nf, -t.warps))
+    # measured order of merit on GB300: D_w near 8R (the largest width whose rings leave room for
+    # 16 warps), 16 warps, two frontlines, clusters of at most 8 x tiles; the model code balance
+    # (Eq. 5) breaks ties
+    def score(t):
+        nclu = -(-s.nx // t.xtile)
+        return (abs(t.dw - 8 * r), -t.warps, -t.nf, nclu > 8, -t.xtile,
+                model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw))
+    out.sort(key=score)
     return out
 
 

@@ -48,7 +48,7 @@ constexpr int BLK_MAXT = 512;    // threads per CTA
 constexpr int MAXCLUSTER = 16;   // x-tiles of one diamond run as one cluster
 
 struct TileMeta {
-    int Lt, t0, ntask, nitem;
+    int Lt, t0, ntask, nitem, nring;
     int clo[MAXLV], chi[MAXLV];        // computed rows (interior), empty: clo == chi
     int nlo[MAXLV], nhi[MAXLV];        // ring rows [nlo, nhi) in [-R, Ny + R)
     int wlo[MAXLV], whi[MAXLV];        // computed rows NOT stored to HBM
@@ -120,6 +120,17 @@ __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.w
 // Shared-memory vector access through 32-bit shared-window addresses.
 template <typename TF, int V> struct Lds;
 template <> struct Lds<float, 4> {
+    // predicated forms: no branch; the load leaves 0 where p is false
+    static __device__ __forceinline__ float ld1_if(bool p, uint32_t a) {
+        float r = 0.f;
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f32 %0, [%2];\n}\n"
+                     : "+f"(r) : "r"((unsigned)p), "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ void st_if(bool p, uint32_t a, const Vec<float, 4>& x) {
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.v4.f32 [%1], {%2, %3, %4, %5};\n}\n"
+                     ::"r"((unsigned)p), "r"(a), "f"(x.v[0]), "f"(x.v[1]), "f"(x.v[2]), "f"(x.v[3]));
+    }
     static __device__ __forceinline__ Vec<float, 4> ld(uint32_t a) {
         Vec<float, 4> r;
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
@@ -132,6 +143,16 @@ template <> struct Lds<float, 4> {
     }
 };
 template <> struct Lds<double, 2> {
+    static __device__ __forceinline__ double ld1_if(bool p, uint32_t a) {
+        double r = 0.0;
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f64 %0, [%2];\n}\n"
+                     : "+d"(r) : "r"((unsigned)p), "r"(a));
+        return r;
+    }
+    static __device__ __forceinline__ void st_if(bool p, uint32_t a, const Vec<double, 2>& x) {
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.shared.v2.f64 [%1], {%2, %3};\n}\n"
+                     ::"r"((unsigned)p), "r"(a), "d"(x.v[0]), "d"(x.v[1]));
+    }
     static __device__ __forceinline__ Vec<double, 2> ld(uint32_t a) {
         Vec<double, 2> r;
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(r.v[0]), "=d"(r.v[1]) : "r"(a));
@@ -166,8 +187,11 @@ struct Item {
     int nr;            // valid rows (1..RB)
     uint32_t ar;       // shared address of rowp
     uint32_t ad[RB];   // shared address of dstp[i] (unused when dstp[i] is null)
+    int rq;            // right-neighbour vector offset (1, or 0 at the end of the ring row)
     bool valid, active, indom, full;
     bool store[RB];
+    bool wr[RB];       // lane writes row i to the next level's ring (fast path)
+    bool fastok;       // warp-uniform: RB real rows and no lane straddles the x boundary
 };
 
 // One tile (row k, diamond b) of one grid, x tile xti, all z; the whole CTA
@@ -266,6 +290,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         }
         M.ntask = ntask;
         M.nitem = nitem;
+        M.nring = off;
         for (int l = 0; l < Lt; ++l) {
             const int t = tlo + l;
             const bool all = (t == P.T - 1) || (l + 1 >= Lt) || (M.chi[l + 1] <= M.clo[l + 1]);
@@ -283,6 +308,16 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     const int Lt = M.Lt;
     if (Lt == 0) return;
     const TF hv = P.halo;
+    if constexpr (PERSIST) {
+        // Dirichlet value everywhere: ring cells of lanes outside the domain are never
+        // written by the fast path and must read as the boundary value
+        VT h;
+#pragma unroll
+        for (int e = 0; e < V; ++e) h.v[e] = hv;
+        const uint32_t rb = smem_u32(ring);
+        for (int i = tid; i < M.nring / V; i += NT) Lds<TF, V>::st(rb + (uint32_t)(i * V * (int)sizeof(TF)), h);
+        __syncthreads();
+    }
     const int ntask = M.ntask;
     const int s_begin = -((2 * R + NF + NF - 1) / NF);
     const int s_end = (Nz - 1 + (Lt - 1) * d) / NF + 1;
@@ -327,6 +362,12 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         I.ar = smem_u32(I.rowp);
 #pragma unroll
         for (int i = 0; i < RB; ++i) I.ad[i] = I.dstp[i] ? smem_u32(I.dstp[i]) : 0u;
+        I.rq = I.qr < 1 ? I.qr : 1;
+#pragma unroll
+        for (int i = 0; i < RB; ++i) I.wr[i] = I.active && I.indom && I.dstp[i] != nullptr;
+        // the fast path writes nothing for lanes outside the domain (the ring is
+        // pre-filled with the Dirichlet value) and has no per-element x mask
+        I.fastok = I.nr == RB && !__any_sync(0xffffffffu, I.indom && !I.full);
     }
 
     if constexpr (PERSIST) {
@@ -458,9 +499,70 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             } else {
                 if (zb + NF <= 0 || zb >= Nz) continue;  // warp-uniform
             }
+            bool fast = false;
+            if constexpr (PERSIST) fast = I.fastok && zb >= 0 && zb + NF + R <= Nz;  // warp-uniform
+            if constexpr (PERSIST) if (fast) {
+                // steady state: every plane of the step and its z + R neighbour are real
+                // planes, both rows are real; straight-line code with predicated accesses
+                constexpr int XB = (int)sizeof(TF);
+                constexpr uint32_t VB = (uint32_t)(V * XB);
+                const uint32_t XsB = (uint32_t)(Xs * XB);
+                const uint32_t PSB = (uint32_t)(I.PS * XB), dPSB = (uint32_t)(I.dPS * XB);
+                int sc = pmod(zb, Q);
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    int sn = sc + R;
+                    if (sn >= Q) sn -= Q;
+                    const uint32_t an = I.ar + (uint32_t)sn * PSB;
+                    win[kk][0][2 * R + f] = Lds<TF, V>::ld(an);
+                    win[kk][1][2 * R + f] = Lds<TF, V>::ld(an + XsB);
+                    const uint32_t acb = I.ar + (uint32_t)sc * PSB;
+                    const VT ydn = Lds<TF, V>::ld(acb - XsB);
+                    const VT yup = Lds<TF, V>::ld(acb + 2 * XsB);
+                    const size_t zoff = (size_t)(zb + f) * gplane;
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        const VT& ctr = win[kk][i][f + R];
+                        const uint32_t ac = acb + (uint32_t)i * XsB;
+                        const TF lf = Lds<TF, V>::ld1_if(lane == 0, ac - (uint32_t)XB);
+                        const TF rt = Lds<TF, V>::ld1_if(lane == 31, ac + (uint32_t)I.rq * VB);
+                        TF xm0 = __shfl_up_sync(0xffffffffu, ctr.v[V - 1], 1);
+                        TF xpl = __shfl_down_sync(0xffffffffu, ctr.v[0], 1);
+                        xm0 = lane == 0 ? lf : xm0;
+                        xpl = lane == 31 ? rt : xpl;
+                        const VT& ym = i == 0 ? ydn : win[kk][0][f + R];
+                        const VT& yp = i == 0 ? win[kk][1][f + R] : yup;
+                        const VT& zp1 = win[kk][i][f + R + 1];
+                        const VT& zm1 = win[kk][i][f + R - 1];
+                        const size_t gidx = I.g0[i] + zoff;  // in bounds for every lane
+                        Vec<TC, V> cv[NC > 0 ? NC : 1];
+                        if constexpr (NC > 0) {
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) cv[m] = ldv_ro<TC, V>(P.C[m] + gidx);
+                        }
+                        VT out;
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const TF xp = e + 1 < V ? ctr.v[e + 1 < V ? e + 1 : 0] : xpl;
+                            const TF xm = e > 0 ? ctr.v[e > 0 ? e - 1 : 0] : xm0;
+                            if constexpr (KIND == K7C) {
+                                out.v[e] = upd7c<TF>(P.c0, P.c1, ctr.v[e], xp, xm, yp.v[e], ym.v[e], zp1.v[e], zm1.v[e]);
+                            } else {
+                                TF c[7];
+#pragma unroll
+                                for (int m = 0; m < 7; ++m) c[m] = Cvt<TF, TC>::f(cv[m < NC ? m : 0].v[e]);
+                                out.v[e] = upd7v<TF>(c, ctr.v[e], xp, xm, yp.v[e], ym.v[e], zp1.v[e], zm1.v[e]);
+                            }
+                        }
+                        Lds<TF, V>::st_if(I.wr[i], I.ad[i] + (uint32_t)sc * dPSB, out);
+                        if (I.store[i]) stv<TF, V>(I.gdst + gidx, out);
+                    }
+                    sc = sc + 1 == Q ? 0 : sc + 1;
+                }
+            }
             const int s0 = pmod(zb, Q);  // ring slot of plane zb
 #pragma unroll
-            for (int f = 0; f < NF; ++f) {
+            for (int f = 0; f < NF && !fast; ++f) {
                 const int z = zb + f;
                 int sc = s0 + f;
                 if (sc >= Q) sc -= Q;  // slot of plane z

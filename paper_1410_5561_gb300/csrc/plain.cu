@@ -5,9 +5,14 @@
 // Thread mapping: a warp covers 32 vectors of V = 16/sizeof(field) consecutive
 // x values (128-bit accesses); a CTA stacks BY warps along y; each thread walks
 // a chunk of z planes and keeps the 2R+1 planes of its own column in a
-// register ring, so each z-neighbour is loaded once. x- and y-neighbours are
-// plain aligned vector loads that hit L1/L2 (they are re-read by the
-// neighbouring threads); coefficients stream through with evict-first loads.
+// register ring, so each z-neighbour is loaded once, plus PF planes loaded
+// ahead so that several HBM loads per thread are in flight. x- and
+// y-neighbours are plain aligned vector loads that hit L1/L2 (they are re-read
+// by the neighbouring threads); coefficients stream through with evict-first
+// loads. The number of z chunks is chosen from the kernel's occupancy so that
+// the CTAs fill whole waves of the GPU.
+#include <mutex>
+
 #include "internal.h"
 
 namespace stg {
@@ -17,7 +22,7 @@ struct CoefPtrs {
     const TC* c[13];
 };
 
-template <int KIND, typename TF, typename TC, int BY>
+template <int KIND, typename TF, typename TC, int BY, int PF>
 __global__ void __launch_bounds__(32 * BY)
 plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, CoefPtrs<TC> C,
                    TF c0, TF c1, int zchunk) {
@@ -38,9 +43,21 @@ plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, C
     Vec<TF, V> ring[2 * R + 1];  // planes k-R .. k+R of this thread's column
 #pragma unroll
     for (int r = 0; r < 2 * R; ++r) ring[r] = ldv<TF, V>(src + base + (ptrdiff_t)(r - R) * (ptrdiff_t)sz);
+    Vec<TF, V> ahead[PF > 0 ? PF : 1];  // planes k+R .. k+R+PF-1 (loaded while k - 1 computes)
+#pragma unroll
+    for (int p = 0; p < PF; ++p)
+        if (k0 + p < k1) ahead[p] = ldv<TF, V>(src + base + (size_t)(R + p) * sz);
 
     for (int k = k0; k < k1; ++k, base += sz) {
-        ring[2 * R] = ldv<TF, V>(src + base + (size_t)R * sz);
+        if constexpr (PF > 0) {
+            ring[2 * R] = ahead[0];
+#pragma unroll
+            for (int p = 0; p + 1 < PF; ++p) ahead[p] = ahead[p + 1];
+            // plane k+R+PF exists (interior or upper halo) while k + PF <= nz - 1
+            if (k + PF < k1) ahead[PF - 1] = ldv<TF, V>(src + base + (size_t)(R + PF) * sz);
+        } else {
+            ring[2 * R] = ldv<TF, V>(src + base + (size_t)R * sz);
+        }
         // x line around the vector: [i0 - J*V, i0 + (J+1)*V)
         TF xl[(2 * J + 1) * V];
 #pragma unroll
@@ -100,29 +117,67 @@ plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, C
     }
 }
 
+// Planes loaded ahead: the constant-coefficient sweep has a single HBM stream per
+// thread and needs the extra loads in flight; the variable-coefficient sweeps
+// already issue n_c + 1 streaming loads per plane.
+template <int KIND> struct PlainPF { static constexpr int v = KIND == K7C ? 3 : 1; };
+
+// Resident CTAs per SM of one kernel instantiation times the SM count, per device
+// (one cache per instantiation: the template arguments name the kernel).
+template <int KIND, typename TF, typename TC, typename KernelT>
+static int plain_slots(KernelT kernel, int threads) {
+    static std::mutex mu;
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (cached[dev] == 0) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess) return 0;
+        cached[dev] = sms * (per > 0 ? per : 1);
+    }
+    return cached[dev];
+}
+
+// z chunks per column: minimise (waves of CTAs) x (planes per chunk + ring warm-up),
+// with chunks of at least 16 planes.
+static int plain_chunks(long long xy, int nz, int R, int slots) {
+    if (slots <= 0) slots = 8 * 152;
+    int best = 1;
+    long long best_cost = -1;
+    const int maxchunks = (nz + 15) / 16 > 0 ? (nz + 15) / 16 : 1;
+    for (int n = 1; n <= maxchunks; ++n) {
+        const int zc = (nz + n - 1) / n;
+        const int nn = (nz + zc - 1) / zc;
+        const long long waves = (xy * nn + slots - 1) / slots;
+        const long long cost = waves * (zc + 2 * R);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = nn;
+        }
+    }
+    return best;
+}
+
 template <int KIND, typename TF, typename TC>
 static cudaError_t launch_plain(const SweepArgs& a, const void* src, void* dst, cudaStream_t s) {
     constexpr int BY = 8;
+    constexpr int PF = PlainPF<KIND>::v;
     constexpr int V = 16 / sizeof(TF);
     const Layout& L = a.L;
     if (L.nx == 0 || L.ny == 0 || L.nz == 0) return cudaSuccess;
     CoefPtrs<TC> C{};
     for (int m = 0; m < KindTraits<KIND>::NC; ++m) C.c[m] = static_cast<const TC*>(a.coef[m]);
+    auto kernel = plain_sweep_kernel<KIND, TF, TC, BY, PF>;
     dim3 block(32, BY);
     unsigned gx = (unsigned)((L.nx + 32 * V - 1) / (32 * V));
     unsigned gy = (unsigned)((L.ny + BY - 1) / BY);
-    // Enough z chunks for about 8 CTAs of 256 threads per SM over 152 SMs,
-    // without making chunks shorter than 16 planes (ring warm-up re-reads 2R planes).
-    long long xy = (long long)gx * gy;
-    int want = (int)((8LL * 152 + xy - 1) / xy);
-    int maxchunks = (L.nz + 15) / 16;
-    int nchunks = want < 1 ? 1 : (want > maxchunks ? maxchunks : want);
-    if (nchunks < 1) nchunks = 1;
-    int zchunk = (L.nz + nchunks - 1) / nchunks;
-    nchunks = (L.nz + zchunk - 1) / zchunk;
+    const int nchunks = plain_chunks((long long)gx * gy, L.nz, KindTraits<KIND>::R, plain_slots<KIND, TF, TC>(kernel, 32 * BY));
+    const int zchunk = (L.nz + nchunks - 1) / nchunks;
     dim3 grid(gx, gy, (unsigned)nchunks);
-    plain_sweep_kernel<KIND, TF, TC, BY><<<grid, block, 0, s>>>(
-        L, static_cast<const TF*>(src), static_cast<TF*>(dst), C, (TF)a.c0, (TF)a.c1, zchunk);
+    kernel<<<grid, block, 0, s>>>(L, static_cast<const TF*>(src), static_cast<TF*>(dst), C, (TF)a.c0, (TF)a.c1,
+                                  zchunk);
     return cudaGetLastError();
 }
 

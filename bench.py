@@ -272,7 +272,7 @@ def traffic_from_profile(kernel_src_hash: str):
 
 def src_hash():
     h = hashlib.sha256()
-    for name in ("blocked.cu", "common.cuh", "internal.h"):
+    for name in ("blocked_impl.cuh", "blocked_launchers.h", "common.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_1410_5561_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()

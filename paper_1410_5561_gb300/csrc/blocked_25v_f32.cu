@@ -1,0 +1,6 @@
+// Blocked-sweep kernels and launchers: 25-point variable-coefficient (Listing 3), FP32.
+#include "blocked_impl.cuh"
+
+namespace stg {
+STG_BLOCKED_LAUNCHERS(, K25V, float, float)
+}  // namespace stg

@@ -67,6 +67,7 @@ struct TileMeta {
     int ldlo[MAXLV], ldhi[MAXLV];      // ring vectors loaded for this level's input
     short tl[MAXTASK], ty[MAXTASK];    // load / fill tasks for interior planes
     unsigned char tfill[MAXTASK];
+    int tpre[MAXTASK + 1];             // vectors of tasks [0, i): a task moves one ring row
     short il[MAXITEM], iy[MAXITEM];    // compute items (level, first row, 32-vector chunk, rows)
     unsigned char ich[MAXITEM], inr[MAXITEM];
 };
@@ -126,9 +127,32 @@ __device__ __forceinline__ void cluster_arrive_relaxed() {
 }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 
+// CTA barrier (__syncthreads) that returns a token: shared-memory loads that take
+// the token as an operand (Lds::ldt) cannot be moved above the barrier, while the
+// compiler stays free to schedule them within the step.
+__device__ __forceinline__ uint32_t bar_sync_token(uint32_t x) {
+    uint32_t t;
+    asm volatile("bar.sync 0;\n\tmov.u32 %0, %1;\n" : "=r"(t) : "r"(x) : "memory");
+    return t;
+}
+
 // Shared-memory vector access through 32-bit shared-window addresses.
 template <typename TF, int V> struct Lds;
 template <> struct Lds<float, 4> {
+    // Loads ordered only by the barrier token tok (data written before that barrier
+    // and not rewritten until the next one): free to be scheduled within a step.
+    static __device__ __forceinline__ Vec<float, 4> ldt(uint32_t a, uint32_t tok) {
+        Vec<float, 4> r;
+        asm("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+            : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "r"(a), "r"(tok));
+        return r;
+    }
+    static __device__ __forceinline__ float ld1t_if(bool p, uint32_t a, uint32_t tok) {
+        float r = 0.f;
+        asm("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f32 %0, [%2];\n}\n"
+            : "+f"(r) : "r"((unsigned)p), "r"(a), "r"(tok));
+        return r;
+    }
     // predicated forms: no branch; the load leaves 0 where p is false
     static __device__ __forceinline__ float ld1_if(bool p, uint32_t a) {
         float r = 0.f;
@@ -152,6 +176,17 @@ template <> struct Lds<float, 4> {
     }
 };
 template <> struct Lds<double, 2> {
+    static __device__ __forceinline__ Vec<double, 2> ldt(uint32_t a, uint32_t tok) {
+        Vec<double, 2> r;
+        asm("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(r.v[0]), "=d"(r.v[1]) : "r"(a), "r"(tok));
+        return r;
+    }
+    static __device__ __forceinline__ double ld1t_if(bool p, uint32_t a, uint32_t tok) {
+        double r = 0.0;
+        asm("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f64 %0, [%2];\n}\n"
+            : "+d"(r) : "r"((unsigned)p), "r"(a), "r"(tok));
+        return r;
+    }
     static __device__ __forceinline__ double ld1_if(bool p, uint32_t a) {
         double r = 0.0;
         asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f64 %0, [%2];\n}\n"
@@ -301,6 +336,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         M.ntask = ntask;
         M.nitem = nitem;
         M.nring = off;
+        M.tpre[0] = 0;
+        for (int i = 0; i < ntask; ++i) M.tpre[i + 1] = M.tpre[i] + (M.ldhi[M.tl[i]] - M.ldlo[M.tl[i]]);
         for (int l = 0; l < Lt; ++l) {
             const int t = tlo + l;
             const bool all = (t == P.T - 1) || (l + 1 >= Lt) || (M.chi[l + 1] <= M.clo[l + 1]);
@@ -318,6 +355,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     const int Lt = M.Lt;
     if (Lt == 0) return;
     const TF hv = P.halo;
+    uint32_t tok = 0;  // barrier token of the fast path's shared-memory loads
     if constexpr (PERSIST) {
         // Dirichlet value everywhere: ring cells of lanes outside the domain are never
         // written by the fast path and must read as the boundary value
@@ -326,7 +364,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         for (int e = 0; e < V; ++e) h.v[e] = hv;
         const uint32_t rb = smem_u32(ring);
         for (int i = tid; i < M.nring / V; i += NT) Lds<TF, V>::st(rb + (uint32_t)(i * V * (int)sizeof(TF)), h);
-        __syncthreads();
+        tok = bar_sync_token(tok);
     }
     const int ntask = M.ntask;
     const int s_begin = -((2 * R + NF + NF - 1) / NF);
@@ -389,44 +427,47 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     }
 
     // ---- producer: HBM loads (cp.async) and Dirichlet fills of planes P_l(s) = [s NF - l d + NF + R, +NF)
-    // Load / fill tasks owned by this warp (tasks warp, warp + NW, ...): the first KT
-    // are kept in registers for the whole sweep (with the ring slot of their next plane,
-    // advanced as the calls proceed), any further ones are re-derived each step.
+    // The (task row, vector) pairs of the tile are spread over all threads, so every
+    // thread moves about the same number of vectors per step: pair q = tid + j NT,
+    // j < KT, is kept in registers for the whole sweep (with the ring slot of its
+    // next plane, advanced as the calls proceed); any further pairs are re-derived.
     constexpr int KT = 2;
-    uint32_t ta_ring[KT];  // shared address: task row, slot 0, this lane's first vector
-    uint32_t ta_psb[KT];   // plane stride of the task's ring (bytes)
-    const TF* ta_src[KT];  // this lane's first vector of the task row at z = 0 (null: fill)
-    int ta_zb0[KT];        // first plane at step 0
-    int ta_nv[KT];         // vectors this lane moves per plane
-    int ta_sl[KT];         // ring slot of the first plane of the next call
+    const int npair = M.tpre[ntask];
+    uint32_t pa_dst[KT];   // shared address: task row, slot 0, the pair's vector
+    uint32_t pa_psb[KT];   // plane stride of the task's ring (bytes)
+    const TF* pa_src[KT];  // the pair's vector of the task row at z = 0 (null: fill)
+    int pa_zb0[KT];        // first plane at step 0
+    int pa_sl[KT];         // ring slot of the first plane of the next call
+    bool pa_ok[KT];
+    {
+        int ti = 0;
 #pragma unroll
-    for (int j = 0; j < KT; ++j) {
-        const int ti = warp + j * NW;
-        ta_nv[j] = 0;
-        ta_zb0[j] = 0;
-        ta_ring[j] = 0;
-        ta_psb[j] = 0;
-        ta_src[j] = nullptr;
-        ta_sl[j] = 0;
-        if (ti >= ntask) continue;
-        const int l = M.tl[ti], y = M.ty[ti];
-        const int nlo = M.nlo[l];
-        const int ldlo = M.ldlo[l], ldhi = M.ldhi[l];
-        const int c0 = ldlo + lane;
-        ta_nv[j] = c0 < ldhi ? (ldhi - c0 + 31) / 32 : 0;
-        ta_psb[j] = (uint32_t)((M.nhi[l] - nlo) * Xs * (int)sizeof(TF));
-        ta_ring[j] = smem_u32(ring + M.roff[l] + (y - nlo) * Xs + c0 * V);
-        ta_zb0[j] = -l * d + NF + R;
-        ta_sl[j] = pmod(s_begin * NF + ta_zb0[j], Q);
-        if (!M.tfill[ti])
-            ta_src[j] = P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH) + (ptrdiff_t)c0 * V;
+        for (int j = 0; j < KT; ++j) {
+            const int q = tid + j * NT;
+            pa_ok[j] = q < npair;
+            pa_dst[j] = 0;
+            pa_psb[j] = 0;
+            pa_src[j] = nullptr;
+            pa_zb0[j] = 0;
+            pa_sl[j] = 0;
+            if (!pa_ok[j]) continue;
+            while (M.tpre[ti + 1] <= q) ++ti;
+            const int l = M.tl[ti], y = M.ty[ti];
+            const int nlo = M.nlo[l];
+            const int c = M.ldlo[l] + (q - M.tpre[ti]);
+            pa_psb[j] = (uint32_t)((M.nhi[l] - nlo) * Xs * (int)sizeof(TF));
+            pa_dst[j] = smem_u32(ring + M.roff[l] + (y - nlo) * Xs + c * V);
+            pa_zb0[j] = -l * d + NF + R;
+            pa_sl[j] = pmod(s_begin * NF + pa_zb0[j], Q);
+            if (!M.tfill[ti])
+                pa_src[j] = P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH) + (ptrdiff_t)c * V;
+        }
     }
     // produce(s) touches the Dirichlet z-halo of some level only if s < fill_lo (the
     // deepest level's planes s NF + NF + R - (Lt - 1) d start below 0) or s >= fill_hi
     // (level 0's planes reach Nz); the per-level test below is exact
     const int fill_lo = cdiv((Lt - 1) * d - NF - R, NF);
     const int fill_hi = fdiv(Nz - 2 * NF - R, NF) + 1;
-    constexpr uint32_t CHB = (uint32_t)(32 * V * sizeof(TF));  // bytes between a lane's vectors
 
     // produce(s) is called for consecutive s (the ring slots advance by N_F per call)
     auto produce = [&](int s) {
@@ -435,27 +476,21 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
         for (int e = 0; e < V; ++e) hvv.v[e] = hv;
 #pragma unroll
         for (int j = 0; j < KT; ++j) {
-            const int z0 = s * NF + ta_zb0[j];
-            if (ta_nv[j] > 0) {
-                const int nv = ta_nv[j];
-                int sl = ta_sl[j];
+            if (pa_ok[j]) {
+                const int z0 = s * NF + pa_zb0[j];
+                int sl = pa_sl[j];
                 if (z0 >= 0 && z0 + NF <= Nz) {  // every plane of the call is a real plane
-                    if (ta_src[j] != nullptr) {
-                        const TF* gp = ta_src[j] + (size_t)z0 * gplane;
+                    if (pa_src[j] != nullptr) {
+                        const TF* gp = pa_src[j] + (size_t)z0 * gplane;
 #pragma unroll
                         for (int fz = 0; fz < NF; ++fz) {
-                            const uint32_t dst = ta_ring[j] + (uint32_t)sl * ta_psb[j];
-                            const TF* g = gp + (size_t)fz * gplane;
-                            cp_async16_u32(dst, g);
-                            if (nv > 1) cp_async16_u32(dst + CHB, g + 32 * V);
-                            for (int c = 2; c < nv; ++c) cp_async16_u32(dst + (uint32_t)c * CHB, g + c * 32 * V);
+                            cp_async16_u32(pa_dst[j] + (uint32_t)sl * pa_psb[j], gp + (size_t)fz * gplane);
                             sl = sl + 1 == Q ? 0 : sl + 1;
                         }
                     } else {
 #pragma unroll
                         for (int fz = 0; fz < NF; ++fz) {
-                            const uint32_t dst = ta_ring[j] + (uint32_t)sl * ta_psb[j];
-                            for (int c = 0; c < nv; ++c) Lds<TF, V>::st(dst + (uint32_t)c * CHB, hvv);
+                            Lds<TF, V>::st(pa_dst[j] + (uint32_t)sl * pa_psb[j], hvv);
                             sl = sl + 1 == Q ? 0 : sl + 1;
                         }
                     }
@@ -463,39 +498,34 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
 #pragma unroll
                     for (int fz = 0; fz < NF; ++fz) {
                         const int z = z0 + fz;
-                        const uint32_t dst = ta_ring[j] + (uint32_t)sl * ta_psb[j];
+                        const uint32_t dst = pa_dst[j] + (uint32_t)sl * pa_psb[j];
                         sl = sl + 1 == Q ? 0 : sl + 1;
                         if (z < 0 || z >= Nz) continue;
-                        if (ta_src[j] == nullptr) {
-                            for (int c = 0; c < nv; ++c) Lds<TF, V>::st(dst + (uint32_t)c * CHB, hvv);
-                        } else {
-                            const TF* g = ta_src[j] + (size_t)z * gplane;
-                            for (int c = 0; c < nv; ++c) cp_async16_u32(dst + (uint32_t)c * CHB, g + c * 32 * V);
-                        }
+                        if (pa_src[j] == nullptr) Lds<TF, V>::st(dst, hvv);
+                        else cp_async16_u32(dst, pa_src[j] + (size_t)z * gplane);
                     }
                 }
             }
-            ta_sl[j] = ta_sl[j] + NF >= Q ? ta_sl[j] + NF - Q : ta_sl[j] + NF;
+            pa_sl[j] = pa_sl[j] + NF >= Q ? pa_sl[j] + NF - Q : pa_sl[j] + NF;
         }
-        for (int ti = warp + KT * NW; ti < ntask; ti += NW) {
+        for (int q = tid + KT * NT, ti = 0; q < npair; q += NT) {
+            while (M.tpre[ti + 1] <= q) ++ti;
             const int l = M.tl[ti], y = M.ty[ti];
-            const bool fill = M.tfill[ti] != 0;
             const int nlo = M.nlo[l];
+            const int c = M.ldlo[l] + (q - M.tpre[ti]);
             const int PS = (M.nhi[l] - nlo) * Xs;
-            TF* rowr = ring + M.roff[l] + (y - nlo) * Xs;
-            const int ldlo = M.ldlo[l], ldhi = M.ldhi[l];
+            TF* rowv = ring + M.roff[l] + (y - nlo) * Xs + c * V;
             const int zb = s * NF - l * d + NF + R;
-            const TF* src = fill ? nullptr : P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH);
 #pragma unroll
             for (int fz = 0; fz < NF; ++fz) {
                 const int z = zb + fz;
                 if (z < 0 || z >= Nz) continue;
-                TF* dst = rowr + pmod(z, Q) * PS;
-                if (fill) {
-                    for (int c = ldlo + lane; c < ldhi; c += 32) stv<TF, V>(dst + c * V, hvv);
+                TF* dst = rowv + pmod(z, Q) * PS;
+                if (M.tfill[ti]) {
+                    stv<TF, V>(dst, hvv);
                 } else {
-                    const TF* gp = src + (size_t)z * gplane;
-                    for (int c = ldlo + lane; c < ldhi; c += 32) cp_async16(dst + c * V, gp + c * V);
+                    const TF* src = P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH) + (ptrdiff_t)c * V;
+                    cp_async16(dst, src + (size_t)z * gplane);
                 }
             }
         }
@@ -556,18 +586,18 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     int sn = sc + R;
                     if (sn >= Q) sn -= Q;
                     const uint32_t an = I.ar + (uint32_t)sn * PSB;
-                    win[kk][0][(2 * R + f + PH * NF) % WIN] = Lds<TF, V>::ld(an);
-                    win[kk][1][(2 * R + f + PH * NF) % WIN] = Lds<TF, V>::ld(an + XsB);
+                    win[kk][0][(2 * R + f + PH * NF) % WIN] = Lds<TF, V>::ldt(an, tok);
+                    win[kk][1][(2 * R + f + PH * NF) % WIN] = Lds<TF, V>::ldt(an + XsB, tok);
                     const uint32_t acb = I.ar + (uint32_t)sc * PSB;
-                    const VT ydn = Lds<TF, V>::ld(acb - XsB);
-                    const VT yup = Lds<TF, V>::ld(acb + 2 * XsB);
+                    const VT ydn = Lds<TF, V>::ldt(acb - XsB, tok);
+                    const VT yup = Lds<TF, V>::ldt(acb + 2 * XsB, tok);
                     const size_t zoff = (size_t)(zb + f) * gplane;
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
                         const VT& ctr = win[kk][i][(f + R + PH * NF) % WIN];
                         const uint32_t ac = acb + (uint32_t)i * XsB;
-                        const TF lf = Lds<TF, V>::ld1_if(lane == 0, ac - (uint32_t)XB);
-                        const TF rt = Lds<TF, V>::ld1_if(lane == 31, ac + (uint32_t)I.rq * VB);
+                        const TF lf = Lds<TF, V>::ld1t_if(lane == 0, ac - (uint32_t)XB, tok);
+                        const TF rt = Lds<TF, V>::ld1t_if(lane == 31, ac + (uint32_t)I.rq * VB, tok);
                         TF xm0 = __shfl_up_sync(0xffffffffu, ctr.v[V - 1], 1);
                         TF xpl = __shfl_down_sync(0xffffffffu, ctr.v[0], 1);
                         xm0 = lane == 0 ? lf : xm0;
@@ -690,6 +720,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     }
                     const size_t gidx = (size_t)I.g0[i] + zoff;
                     Vec<TC, V> cv[NC > 0 ? NC : 1];
+                    (void)cv;
                     if constexpr (NC > 0) {
                         if (I.active && I.indom) {
 #pragma unroll
@@ -751,7 +782,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             }
         }
         cp_async_wait_1();
-        __syncthreads();
+        tok = bar_sync_token(tok + 1);
         if (lock) cluster_arrive_relaxed();
     };
 
@@ -963,6 +994,7 @@ static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps
     const int rb = R == 1 ? 2 : 1;
     int items = item_bound(dw, R) / rb * s.nch;
     if (items > MAXITEM) return s;
+    if (ring_rows_bound(dw, R) > MAXTASK) return s;  // load / fill tasks are ring rows
     int K = (items + warps - 1) / warps;
     if (K > 4) return s;
     s.K = K <= 1 ? 1 : (K <= 2 ? 2 : 4);

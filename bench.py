@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GLUP/s and ncu HBM bytes/LUP, blocked vs plain sweep on one GB300, per stencil"
 HEADLINE = dict(kind="7pt_const", n=1024, fdt="f32", cdt=None, T=100)
-PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "blocked_kernel_7pt_const_f32_traffic.txt")
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "blocked_persist_kernel_7pt_const_f32_traffic.txt")
 CPU_SAMPLE_N = 256
 CPU_BASELINE_N = 512
 
@@ -85,10 +85,15 @@ def cpu_oracle_sample(budget_s: float = 15.0, n: int = CPU_BASELINE_N, seed: int
     from paper_1410_5561_gb300 import inputs
     u0 = inputs.field_u0(seed, n, n, n)
     oracle.sweep("7pt_const", u0, 1)  # first call: thread pool start-up, page faults
+    # per-step time from the difference of two runs (each call also pads and copies the grid)
     t0 = time.perf_counter()
     oracle.sweep("7pt_const", u0, 2)
-    t1 = max((time.perf_counter() - t0) / 2, 1e-4)
-    T = max(1, min(1000, int(budget_s / t1)))
+    t2 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.sweep("7pt_const", u0, 6)
+    t6 = time.perf_counter() - t0
+    t1 = max((t6 - t2) / 4, 1e-4)
+    T = max(1, min(1000, int(max(budget_s - (t2 - 2 * t1), 1.0) / t1)))
     t0 = time.perf_counter()
     oracle.sweep("7pt_const", u0, T)
     dt = time.perf_counter() - t0
@@ -467,7 +472,7 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
         s.set_tuning("plain")
         tp = timed(s, T, 2, 1) / 2
         try:
-            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=5)
+            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
             tb = timed(s, T, 2, 1) / 2
             tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
             bb = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)

@@ -53,11 +53,19 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
     fdt = _DT_NAME[s.dtype]
     cdt = _DT_NAME[s.coef_dtype]
     # measured order of merit on GB300: D_w near 8R (the largest width whose rings leave room for
-    # 16 warps), 16 warps, two frontlines, clusters of at most 8 x tiles; the model code balance
-    # (Eq. 5) breaks ties
+    # 16 warps), 16 warps, two frontlines, then the share of computed x columns that are useful
+    # (each x tile computes whole 32-vector chunks of its row, overlap included); the model code
+    # balance (Eq. 5) breaks ties
+    def chunks(t):
+        lt = t.dw // r - 1
+        ov = -(-r * (lt - 1) // v) if lt > 1 else 0
+        return -(-(t.xtile // v + 2 * ov) // 32)
+
+    def useful(t):
+        return s.nx / (-(-s.nx // t.xtile) * chunks(t) * 32 * v)
+
     def score(t):
-        nclu = -(-s.nx // t.xtile)
-        return (abs(t.dw - 8 * r), -t.warps, -t.nf, nclu > 8, -t.xtile,
+        return (abs(t.dw - 8 * r), -t.warps, -t.nf, -round(useful(t), 3), chunks(t), -t.xtile,
                 model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw))
     out.sort(key=score)
     return out

@@ -497,11 +497,12 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
 
 def batched(device, seed):
     """64 independent 7-point variable FP32 grids (sides 32..192, T 10..200): one persistent
-    CUDA-graph launch vs one (persistent blocked) launch per grid."""
+    CUDA-graph launch (autotuned diamond width, frontlines and warps) vs one launch per grid
+    (plain sweeps, T launches per grid; and the blocked sweep with each grid's first tuner
+    candidate)."""
     import torch
-    from paper_1410_5561_gb300 import inputs
+    from paper_1410_5561_gb300 import inputs, tuner
     from paper_1410_5561_gb300.batch import Batch
-    from paper_1410_5561_gb300.stencil import Tuning
     shapes = inputs.batch_shapes(seed)
     grids = []
     for q, (nx, ny, nz, T) in enumerate(shapes):
@@ -509,7 +510,7 @@ def batched(device, seed):
         grids.append(s)
     Ts = [sh[3] for sh in shapes]
     lups = sum(nx * ny * nz * T for (nx, ny, nz, T) in shapes)
-    tn = Tuning(8, 1, 16, 0)
+    tn, table = tuner.tune_batch(grids, Ts)
     b = Batch(grids, Ts, tn)
     b.launch()
     torch.cuda.synchronize(device)
@@ -527,22 +528,32 @@ def batched(device, seed):
     t_batch = e0.elapsed_time(e1) / 1e3 / reps
     b.sync_parity()
     status = b.status()
-    # one launch per grid, each with the same tuning (x tile = whole row)
-    for s, (nx, ny, nz, T) in zip(grids, shapes):
-        s.set_tuning("blocked", Tuning(8, 1, 16, ((nx + 3) // 4) * 4))
-        s.run(T)
-    torch.cuda.synchronize(device)
     stream = torch.cuda.current_stream(device)
-    e0.record(stream)
-    for _ in range(reps):
+
+    def per_grid(reps_):
         for s, T in zip(grids, Ts):
             s.run(T)
-    e1.record(stream)
-    e1.synchronize()
-    t_each = e0.elapsed_time(e1) / 1e3 / reps
-    return {"grids": len(shapes), "lups": lups, "tuning": {"dw": 8, "nf": 1, "warps": 16},
-            "graph_launch_glups": lups / t_batch / 1e9, "per_grid_launches_glups": lups / t_each / 1e9,
-            "graph_ms": 1e3 * t_batch, "per_grid_ms": 1e3 * t_each, "tiles": b.items, "status": status}
+        torch.cuda.synchronize(device)
+        e0.record(stream)
+        for _ in range(reps_):
+            for s, T in zip(grids, Ts):
+                s.run(T)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps_
+
+    for s in grids:  # one launch per grid and step
+        s.set_tuning("plain")
+    t_plain = per_grid(2)
+    for s in grids:  # one persistent blocked launch per grid
+        s.set_tuning("blocked", tuner.candidates(s)[0])
+    t_blk = per_grid(1)
+    return {"grids": len(shapes), "lups": lups, "tuning": {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps},
+            "graph_launch_glups": lups / t_batch / 1e9, "graph_ms": 1e3 * t_batch,
+            "per_grid_plain_glups": lups / t_plain / 1e9, "per_grid_plain_ms": 1e3 * t_plain,
+            "per_grid_blocked_glups": lups / t_blk / 1e9, "per_grid_blocked_ms": 1e3 * t_blk,
+            "autotune": [{"tuning": f"dw={c.dw} nf={c.nf} warps={c.warps}", "ms": 1e3 * t} for c, t in table],
+            "tiles": b.items, "status": status}
 
 
 def adjoint_timing(device, seed):

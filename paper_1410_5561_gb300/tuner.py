@@ -143,3 +143,45 @@ def best_blocked(s: Stencil, T: int, reps: int = 2, max_candidates: int = 10):
     s.set_tuning("blocked", best[1])
     _CACHE[key] = (best[1], table)
     return best[1], table
+
+
+BATCH_CANDIDATES = [Tuning(dw, nf, w, 0) for dw in (4, 6, 8) for nf in (1, 2) for w in (8, 16)] + \
+    [Tuning(4, 1, 4, 0), Tuning(2, 1, 4, 0), Tuning(2, 1, 8, 0)]
+
+
+def tune_batch(grids: list[Stencil], T: list[int], candidates=None, reps: int = 2):
+    """Fastest batch tuning (x tiles are whole rows in a batch) for advancing ``grids`` by ``T``.
+
+    Each feasible candidate is built as a Batch, captured in a CUDA graph and replayed; the
+    grids advance while timing (callers reset them). Returns (tuning, table of (tuning, seconds)).
+    Section II-A: the paper tunes the diamond width and thread-group size per stencil and machine;
+    here the small, uneven grids of a batch favour narrower diamonds than one large grid.
+    """
+    from .batch import Batch
+    table = []
+    best = (float("inf"), None)
+    for tn in (candidates or BATCH_CANDIDATES):
+        try:
+            b = Batch(grids, T, tn)
+        except Exception:
+            continue
+        g = b.capture()
+        g.replay()
+        torch.cuda.synchronize(grids[0].device)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        b.sync_parity()
+        del g
+        b.close()
+        table.append((tn, t))
+        if t < best[0]:
+            best = (t, tn)
+    if best[1] is None:
+        raise RuntimeError("no feasible batch tuning")
+    return best[1], table

@@ -155,3 +155,42 @@ def test_full_size_25pt_adjoint_dot_product_fp32():
     assert abs(lhs - rhs) <= 1e-4 * (float(y.detach().double().norm()) * float(lam.double().norm()))
     assert s.last_coef_grad.shape == (13, n, n, n)
     assert torch.isfinite(s.last_coef_grad).all()
+
+
+def test_single_step_gradient_is_exact_product_fp32():
+    """T = 1: gC_m(p) = lambda_1(p) u_0(p + o_m), a product of two FP32 values and exact in
+    FP64. Pins the FP32 -> FP64 conversion of the gradient update bit for bit, with
+    subnormals, signed zeros and large values planted in both factors."""
+    import torch
+    p = Problem("7pt_var", 37, 9, 7, fdt="f32", seed=5)
+    s = p.make()
+    u0 = p.u0.astype(np.float32)
+    f = u0.reshape(-1)
+    f[::11] = np.float32(1e-40)
+    f[3::17] = np.float32(-3e-42)
+    f[5::23] = np.float32(0.0)
+    f[7::29] = np.float32(-0.0)
+    f[9::31] = np.float32(3e30)
+    s.set_field(torch.from_numpy(u0).cuda(), halo=0.0)
+    lam = inputs.uniform(9, 0, u0.shape, -1, 1).astype(np.float32)
+    g = lam.reshape(-1)
+    g[2::13] = np.float32(2e-39)
+    g[4::19] = np.float32(-0.0)
+    ws = s.adjoint_workspace(1, 1)
+    s.run_checkpointed(1, 1, ws)
+    lam_t = s.new_field_array(zero=True)
+    s.interior_of(lam_t).copy_(torch.from_numpy(lam).cuda())
+    gu = s.new_field_array(zero=False)
+    gc = [s.new_grad_array() for _ in range(7)]
+    s.run_adjoint(1, 1, lam_t, gu, gc, ws)
+    torch.cuda.synchronize()
+    up = np.zeros((u0.shape[0] + 2, u0.shape[1] + 2, u0.shape[2] + 2))
+    up[1:-1, 1:-1, 1:-1] = u0.astype(np.float64)
+    nz, ny, nx = u0.shape
+    # neighbour weighed by C_m (Listing 2 order: centre, +x, -x, +y, -y, +z, -z), axes (z, y, x)
+    offs = [(0, 0, 0), (0, 0, 1), (0, 0, -1), (0, 1, 0), (0, -1, 0), (1, 0, 0), (-1, 0, 0)]
+    for m, (dz, dy, dx) in enumerate(offs):
+        nb = up[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+        want = lam.astype(np.float64) * nb + 0.0  # accumulated onto +0: a -0 product reads +0
+        got = s.interior_of(gc[m]).cpu().numpy()
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), m

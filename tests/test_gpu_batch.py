@@ -95,3 +95,24 @@ def test_batch_full_workload_sampled():
     for q in (0, 7, 21, 42, 63):
         p, T = probs[q]
         assert np.array_equal(grids[q].get_field().cpu().numpy(), _plain_result(p, T)), q
+
+
+def test_batch_autotuner_choice_is_feasible_and_exact():
+    """tuner.tune_batch times the candidates as graph replays and returns one that builds;
+    a fresh batch with it reproduces every grid's plain sweep bit for bit."""
+    from paper_1410_5561_gb300 import tuner
+    from paper_1410_5561_gb300.batch import Batch
+    from paper_1410_5561_gb300.stencil import Tuning
+    probs = _problems()
+    grids = [p.make() for p, _ in probs]
+    Ts = [T for _, T in probs]
+    cands = [Tuning(4, 1, 8, 0), Tuning(8, 2, 16, 0), Tuning(6, 1, 16, 0), Tuning(64, 8, 8, 0)]
+    tn, table = tuner.tune_batch(grids, Ts, cands, reps=1)
+    assert tn in cands and len(table) >= 1 and all(t > 0 for _, t in table)
+    assert all(c != Tuning(64, 8, 8, 0) for c, _ in table)  # infeasible: skipped
+    fresh = [p.make() for p, _ in probs]
+    b = Batch(fresh, Ts, tn)
+    b.launch()
+    assert b.status() == 0
+    for (p, T), g in zip(probs, fresh):
+        assert np.array_equal(g.get_field().cpu().numpy(), _plain_result(p, T))

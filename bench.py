@@ -283,31 +283,68 @@ def src_hash():
     return h.hexdigest()
 
 
+class Ranks:
+    """The processes of one launch (torchrun sets WORLD_SIZE, RANK, LOCAL_RANK, MASTER_*):
+    one per GPU, each running its own replica of the workload. Only a barrier and the
+    max-over-ranks of a time cross ranks; nothing of the sweep is exchanged."""
+
+    def __init__(self, backend: str = "nccl"):
+        import torch
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        self.dist = None
+        if backend == "nccl":
+            if self.world > 1:
+                torch.cuda.set_device(self.local)
+            self.device = torch.device("cuda", self.local if self.world > 1 else torch.cuda.current_device())
+        else:
+            self.device = torch.device("cpu")
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    @property
+    def root(self) -> bool:
+        return self.rank == 0
+
+    def barrier(self):
+        if self.dist is None:
+            return
+        if self.backend == "nccl":
+            self.dist.barrier(device_ids=[self.device.index])
+        else:
+            self.dist.barrier()
+
+    def maxall(self, x: float) -> float:
+        """max over ranks (a time: the job ends when its slowest rank does)"""
+        if self.dist is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def aggregate(self, units_per_rank: float, seconds: float) -> float:
+        """Whole-job throughput: the units all ranks processed over the max-over-ranks time."""
+        return self.world * units_per_rank / self.maxall(seconds)
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def run_ours(args):
     import torch
     from paper_1410_5561_gb300 import model, tuner
     from paper_1410_5561_gb300.stencil import probe_fma_peak
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    device = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
-
-    def barrier():
-        if dist is not None:
-            dist.barrier(device_ids=[device.index])
-
-    def maxall(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl")
+    world, rank, device = ranks.world, ranks.rank, ranks.device
+    barrier, maxall = ranks.barrier, ranks.maxall
 
     hbm_peak, peak_src = peaks()
     fp32_peak = probe_fma_peak(torch.float32, device=device)
@@ -446,9 +483,8 @@ def run_ours(args):
                 torch.cuda.empty_cache()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier(device_ids=[device.index])
-        dist.destroy_process_group()
+    ranks.barrier()
+    ranks.close()
     return 0
 
 

@@ -431,7 +431,9 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     // thread moves about the same number of vectors per step: pair q = tid + j NT,
     // j < KT, is kept in registers for the whole sweep (with the ring slot of its
     // next plane, advanced as the calls proceed); any further pairs are re-derived.
-    constexpr int KT = 2;
+    // (one pair per thread covers the 7-point variable tiles and frees registers for
+    // their coefficient loads; measured on GB300)
+    constexpr int KT = KIND == K7V ? 1 : 2;
     const int npair = M.tpre[ntask];
     uint32_t pa_dst[KT];   // shared address: task row, slot 0, the pair's vector
     uint32_t pa_psb[KT];   // plane stride of the task's ring (bytes)

@@ -54,6 +54,23 @@ def test_blocked_bitwise_equals_plain_r4(shape, fdt, tn, T):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("kind,shape,fdt,cdt,tn", [
+    ("7pt_const", (245, 26, 20), "f32", None, Tuning(8, 2, 16, 116)),
+    ("7pt_var", (233, 18, 15), "f32", None, Tuning(8, 1, 16, 116)),
+    ("7pt_var", (240, 21, 13), "f32", "bf16", Tuning(8, 2, 16, 116)),
+    ("7pt_const", (251, 22, 17), "f32", None, Tuning(4, 1, 4, 124)),
+    ("7pt_const", (110, 20, 12), "f64", None, Tuning(8, 2, 16, 52)),
+])
+@pytest.mark.parametrize("T", [1, 7, 13])
+def test_blocked_wide_x_tiles_bitwise(kind, shape, fdt, cdt, tn, T):
+    """x tiles at and just past the width one 32-vector chunk holds (tile rows of one and
+    of two chunks), several tiles per row, a partial last tile."""
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=14, halo=0.5)
+    a = _run(p, T, "plain")
+    b = _run(p, T, "blocked", tn)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("kind,shape,fdt,T,tn", [
     ("7pt_const", (64, 64, 64), "f64", 8, Tuning(8, 1, 8, 48)),
     ("7pt_const", (64, 64, 64), "f64", 8, Tuning(10, 1, 16, 16)),

@@ -615,6 +615,17 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
 #pragma unroll
                             for (int m = 0; m < NC; ++m) cv[m] = ldv_ro<TC, V>(P.C[m] + gidx);
                         }
+                        if constexpr (NC > 0 && sizeof(TC) < sizeof(TF)) {
+                            // BF16 coefficients: ask L2 for this row's coefficients N_F planes
+                            // ahead (the item's next step), so that the first level touching a
+                            // plane does not wait on HBM; measured +23 % on GB300 (no gain for
+                            // FP32 coefficients, whose kernel is short of registers instead).
+                            // In bounds: z + N_F + R <= Nz - 1 + N_F < Nz + 2R planes.
+                            static_assert(NF <= 2 * R, "prefetch plane inside the array");
+#pragma unroll
+                            for (int m = 0; m < NC; ++m)
+                                asm volatile("prefetch.global.L2 [%0];" ::"l"(P.C[m] + gidx + (size_t)NF * gplane));
+                        }
                         VT out;
 #pragma unroll
                         for (int e = 0; e < V; ++e) {

@@ -124,9 +124,11 @@ int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* ar
 int stencil_set_field(stencil_t h, const void* src, double halo_value, int where);
 
 /* Select the schedule used by run(): STENCIL_PLAIN (one launch per step),
- * STENCIL_BLOCKED with *tuning (NULL: library default), or STENCIL_AUTO (the
- * library default blocked tuning when it fits, else plain). Returns
- * STENCIL_ENOSMEM / STENCIL_EINVAL for an infeasible blocked tuning. */
+ * STENCIL_BLOCKED with *tuning (NULL: library default: D_w = 8R, N_F = 2 where it
+ * fits, 16 warps for R = 1, the widest x tile whose rows fit one warp of vectors), or
+ * STENCIL_AUTO (plain for FP64 fields and the 25-point stencil, where the plain sweep
+ * measured faster on GB300; else the default blocked tuning when it fits, else plain).
+ * Returns STENCIL_ENOSMEM / STENCIL_EINVAL for an infeasible blocked tuning. */
 int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning);
 
 /* Advance the current field by T >= 0 Jacobi steps (Listings 1-3 applied T

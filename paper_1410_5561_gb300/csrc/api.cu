@@ -54,7 +54,7 @@ static BlockedTune default_tune(const stencil_grid* h) {
     int R = kind_radius(h->kind);
     int eb = dtype_bytes(h->fdt);
     t.dw = R == 1 ? 8 : 16;
-    t.nf = 1;
+    t.nf = 2;
     t.warps = R == 1 ? 16 : 8;
     {
         // widest x tile whose bottom level (tile plus trapezoid overlap) fits one warp of vectors
@@ -67,7 +67,12 @@ static BlockedTune default_tune(const stencil_grid* h) {
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 0;
     SweepArgs a = args_of(h);
-    while (t.dw > 2 * R && (blocked_smem_bytes(a, t) == 0 || blocked_smem_bytes(a, t) > (size_t)optin)) t.dw /= 2;
+    auto fits = [&](const BlockedTune& x) {
+        const size_t b = blocked_smem_bytes(a, x);
+        return b != 0 && b <= (size_t)optin;
+    };
+    if (!fits(t)) t.nf = 1;
+    while (t.dw > 2 * R && !fits(t)) t.dw /= 2;
     return t;
 }
 
@@ -248,6 +253,13 @@ int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning) {
         return STENCIL_OK;
     }
     if (scheme != STENCIL_BLOCKED && scheme != STENCIL_AUTO) return STENCIL_EINVAL;
+    if (scheme == STENCIL_AUTO && (h->fdt == DT_F64 || h->kind == STENCIL_25PT_VAR)) {
+        // Measured on GB300: FP64 sweeps are bound by the FP64 units (1/60 of the FP32 rate),
+        // where the blocked sweep's x-tile overlap only adds work, and the 25-point rings fit
+        // only narrow x tiles; the plain sweep is faster for both.
+        h->scheme = STENCIL_PLAIN;
+        return STENCIL_OK;
+    }
     BlockedTune t = default_tune(h);
     if (tuning && scheme == STENCIL_BLOCKED) {
         t.dw = tuning->dw;

@@ -152,3 +152,22 @@ def test_persistent_plan_larger_than_workspace_is_split():
     a = _run(p, 300, "plain")
     b = _run(p, 300, "blocked", Tuning(2, 1, 4, 4))
     assert np.array_equal(a, b)
+
+
+def test_auto_scheme_and_default_tuning():
+    """STENCIL_AUTO: the plain sweep for FP64 and the 25-point stencil, the default blocked
+    tuning otherwise (N_F = 2 where it fits); both give the plain sweep's result."""
+    for kind, fdt, cdt, blocked in [("7pt_const", "f32", None, True), ("7pt_var", "f32", "bf16", True),
+                                    ("7pt_const", "f64", None, False), ("25pt_var", "f32", None, False)]:
+        p = Problem(kind, 70, 23, 19, fdt=fdt, cdt=cdt, seed=16)
+        s = p.make()
+        s.set_tuning("auto")
+        n0 = s.launches
+        s.run(9)
+        launches = s.launches - n0
+        assert (launches == 1) == blocked, (kind, fdt, launches)  # persistent blocked: one launch
+        assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 9, "plain")), (kind, fdt)
+        d = p.make()
+        d.set_tuning("blocked")  # library default tuning
+        d.run(9)
+        assert np.array_equal(d.get_field().cpu().numpy(), _run(p, 9, "plain")), (kind, fdt)

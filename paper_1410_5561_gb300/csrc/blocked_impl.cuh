@@ -147,6 +147,11 @@ template <> struct Lds<float, 4> {
             : "=f"(r.v[0]), "=f"(r.v[1]), "=f"(r.v[2]), "=f"(r.v[3]) : "r"(a), "r"(tok));
         return r;
     }
+    static __device__ __forceinline__ float ld1t(uint32_t a, uint32_t tok) {
+        float r;
+        asm("ld.shared.f32 %0, [%1];\n" : "=f"(r) : "r"(a), "r"(tok));
+        return r;
+    }
     static __device__ __forceinline__ float ld1t_if(bool p, uint32_t a, uint32_t tok) {
         float r = 0.f;
         asm("{\n .reg .pred q;\n setp.ne.u32 q, %1, 0;\n @q ld.shared.f32 %0, [%2];\n}\n"
@@ -179,6 +184,11 @@ template <> struct Lds<double, 2> {
     static __device__ __forceinline__ Vec<double, 2> ldt(uint32_t a, uint32_t tok) {
         Vec<double, 2> r;
         asm("ld.shared.v2.f64 {%0, %1}, [%2];\n" : "=d"(r.v[0]), "=d"(r.v[1]) : "r"(a), "r"(tok));
+        return r;
+    }
+    static __device__ __forceinline__ double ld1t(uint32_t a, uint32_t tok) {
+        double r;
+        asm("ld.shared.f64 %0, [%1];\n" : "=d"(r) : "r"(a), "r"(tok));
         return r;
     }
     static __device__ __forceinline__ double ld1t_if(bool p, uint32_t a, uint32_t tok) {
@@ -216,6 +226,7 @@ __device__ __forceinline__ int fdiv(int a, int b) { return a >= 0 ? a / b : -((-
 __device__ __forceinline__ int cdiv(int a, int b) { return -fdiv(-a, b); }
 __device__ __forceinline__ int wrap_inc(int s, int q) { return s + 1 == q ? 0 : s + 1; }
 constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+
 
 // Per-warp state of one owned item (level l, RB adjacent rows y0.., one 32-vector
 // chunk): pointers and lane flags.
@@ -598,12 +609,25 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     for (int i = 0; i < 2; ++i) {
                         const VT& ctr = win[kk][i][(f + R + PH * NF) % WIN];
                         const uint32_t ac = acb + (uint32_t)i * XsB;
-                        const TF lf = Lds<TF, V>::ld1t_if(lane == 0, ac - (uint32_t)XB, tok);
-                        const TF rt = Lds<TF, V>::ld1t_if(lane == 31, ac + (uint32_t)I.rq * VB, tok);
-                        TF xm0 = __shfl_up_sync(0xffffffffu, ctr.v[V - 1], 1);
-                        TF xpl = __shfl_down_sync(0xffffffffu, ctr.v[0], 1);
-                        xm0 = lane == 0 ? lf : xm0;
-                        xpl = lane == 31 ? rt : xpl;
+                        // x neighbours of the lane's first and last element. Variable
+                        // coefficients: straight from the ring row (fewer issue slots than
+                        // shuffles plus edge loads; the word before a chunk's first vector is
+                        // in the shared window and only feeds columns outside the level's
+                        // range). Constant coefficients: shuffles, with the edge lanes'
+                        // neighbours loaded (the direct loads' 4-way bank conflicts cost this
+                        // shared-memory-heavier kernel more than they save; measured).
+                        TF xm0, xpl;
+                        if constexpr (NC > 0) {
+                            xm0 = Lds<TF, V>::ld1t(ac - (uint32_t)XB, tok);
+                            xpl = Lds<TF, V>::ld1t(ac + (uint32_t)I.rq * VB, tok);
+                        } else {
+                            const TF lf = Lds<TF, V>::ld1t_if(lane == 0, ac - (uint32_t)XB, tok);
+                            const TF rt = Lds<TF, V>::ld1t_if(lane == 31, ac + (uint32_t)I.rq * VB, tok);
+                            xm0 = __shfl_up_sync(0xffffffffu, ctr.v[V - 1], 1);
+                            xpl = __shfl_down_sync(0xffffffffu, ctr.v[0], 1);
+                            xm0 = lane == 0 ? lf : xm0;
+                            xpl = lane == 31 ? rt : xpl;
+                        }
                         const VT& ym = i == 0 ? ydn : win[kk][0][(f + R + PH * NF) % WIN];
                         const VT& yp = i == 0 ? win[kk][1][(f + R + PH * NF) % WIN] : yup;
                         const VT& zp1 = win[kk][i][(f + R + 1 + PH * NF) % WIN];

@@ -22,8 +22,21 @@ struct CoefPtrs {
     const TC* c[13];
 };
 
+// Per stencil and element types: planes loaded ahead (PF) and the CTAs per SM the register
+// allocation must allow (MINB), chosen by measurement on GB300. The constant-coefficient
+// sweep has a single HBM stream per thread and wants loads in flight; the variable ones
+// issue n_c + 1 streaming loads per plane already and are limited by the registers their
+// coefficient vectors take (the 25-point BF16 / FP64 sweeps double their speed at 2 CTAs).
+template <int KIND, typename TF, typename TC> struct PlainCfg { static constexpr int PF = 1, MINB = 1; };
+template <typename TF> struct PlainCfg<K7C, TF, TF> { static constexpr int PF = 3, MINB = 5; };
+template <> struct PlainCfg<K7V, float, float> { static constexpr int PF = 0, MINB = 3; };
+template <> struct PlainCfg<K7V, double, double> { static constexpr int PF = 0, MINB = 3; };
+template <> struct PlainCfg<K25V, float, float> { static constexpr int PF = 0, MINB = 1; };
+template <> struct PlainCfg<K25V, float, __nv_bfloat16> { static constexpr int PF = 1, MINB = 2; };
+template <> struct PlainCfg<K25V, double, double> { static constexpr int PF = 1, MINB = 2; };
+
 template <int KIND, typename TF, typename TC, int BY, int PF>
-__global__ void __launch_bounds__(32 * BY)
+__global__ void __launch_bounds__(32 * BY, (PlainCfg<KIND, TF, TC>::MINB))
 plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, CoefPtrs<TC> C,
                    TF c0, TF c1, int zchunk) {
     constexpr int R = KindTraits<KIND>::R;
@@ -117,11 +130,6 @@ plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, C
     }
 }
 
-// Planes loaded ahead: the constant-coefficient sweep has a single HBM stream per
-// thread and needs the extra loads in flight; the variable-coefficient sweeps
-// already issue n_c + 1 streaming loads per plane.
-template <int KIND> struct PlainPF { static constexpr int v = KIND == K7C ? 3 : 1; };
-
 // Resident CTAs per SM of one kernel instantiation times the SM count, per device
 // (one cache per instantiation: the template arguments name the kernel).
 template <int KIND, typename TF, typename TC, typename KernelT>
@@ -163,7 +171,7 @@ static int plain_chunks(long long xy, int nz, int R, int slots) {
 template <int KIND, typename TF, typename TC>
 static cudaError_t launch_plain(const SweepArgs& a, const void* src, void* dst, cudaStream_t s) {
     constexpr int BY = 8;
-    constexpr int PF = PlainPF<KIND>::v;
+    constexpr int PF = PlainCfg<KIND, TF, TC>::PF;
     constexpr int V = 16 / sizeof(TF);
     const Layout& L = a.L;
     if (L.nx == 0 || L.ny == 0 || L.nz == 0) return cudaSuccess;

@@ -189,6 +189,21 @@ int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, v
 
 static cudaError_t copy_interior(const stencil_grid* h, int eb, const void* dense, void* padded, bool to_padded) {
     const Layout& L = h->L;
+    // device memory, or page-locked host memory the device can address: the library's copy
+    // kernel; pageable host memory: a pitched DMA
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, dense) == cudaSuccess) {
+        const void* dp = nullptr;
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) dp = dense;
+        else if (at.type == cudaMemoryTypeHost) dp = at.devicePointer;
+        if (dp) {
+            cudaError_t e = to_padded ? copy_rows(L, eb, dp, padded, true, h->stream)
+                                      : copy_rows(L, eb, padded, const_cast<void*>(dp), false, h->stream);
+            return e;
+        }
+    } else {
+        cudaGetLastError();  // not a CUDA pointer: clear the error, use the DMA below
+    }
     cudaMemcpy3DParms p{};
     cudaPitchedPtr dn = make_cudaPitchedPtr(const_cast<void*>(dense), (size_t)L.nx * eb, (size_t)L.nx, (size_t)L.ny);
     cudaPitchedPtr pd = make_cudaPitchedPtr(padded, (size_t)L.px * eb, (size_t)L.px, (size_t)L.py);

@@ -41,6 +41,8 @@ cudaError_t plain_step(const SweepArgs& a, const void* src, void* dst, cudaStrea
 
 // Fill n elements of dtype dt at p with value v.
 cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s);
+// Dense interior rows <-> padded layout (src/dst device or device-mapped host pointers).
+cudaError_t copy_rows(const Layout& L, int eb, const void* src, void* dst, bool to_padded, cudaStream_t s);
 
 // Temporally blocked run of T steps from parity p0 (array (p0 + t) & 1 holds u_t).
 // Returns cudaErrorInvalidValue for an infeasible tuning, after checking it on the host.

@@ -218,6 +218,39 @@ __global__ void fill_kernel(T* __restrict__ p, size_t n, T v) {
         p[i] = v;
 }
 
+// ------------------------------------------------------------------ interior copy
+// Dense (nz, ny, nx) rows <-> the padded layout's interior rows. Either side may be device
+// memory or page-locked host memory mapped into the device's address space (read and written
+// over the host link by the kernel's own loads and stores, which keeps many 16-byte accesses
+// in flight: faster than a pitched DMA of short rows). One CTA per row, 16-byte accesses when
+// both row starts and the row length allow, else elementwise.
+__global__ void copy_rows_kernel(const char* __restrict__ src, char* __restrict__ dst, Layout L, int eb,
+                                 int to_padded) {
+    const size_t rows = (size_t)L.ny * L.nz;
+    const size_t rb = (size_t)L.nx * eb;
+    for (size_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int y = (int)(r % (size_t)L.ny), z = (int)(r / (size_t)L.ny);
+        const size_t pad = L.at(0, y, z) * (size_t)eb;
+        const char* a = src + (to_padded ? r * rb : pad);
+        char* b = dst + (to_padded ? pad : r * rb);
+        if ((((uintptr_t)a | (uintptr_t)b | rb) & 15u) == 0) {
+            for (size_t i = threadIdx.x; i < rb / 16; i += blockDim.x)
+                reinterpret_cast<uint4*>(b)[i] = reinterpret_cast<const uint4*>(a)[i];
+        } else {
+            for (size_t i = threadIdx.x; i < rb; i += blockDim.x) b[i] = a[i];
+        }
+    }
+}
+
+cudaError_t copy_rows(const Layout& L, int eb, const void* src, void* dst, bool to_padded, cudaStream_t s) {
+    const size_t rows = (size_t)L.ny * L.nz;
+    if (rows == 0 || L.nx == 0) return cudaSuccess;
+    unsigned blocks = rows < (size_t)152 * 16 ? (unsigned)rows : 152u * 16u;
+    copy_rows_kernel<<<blocks, 256, 0, s>>>(static_cast<const char*>(src), static_cast<char*>(dst), L, eb,
+                                            to_padded ? 1 : 0);
+    return cudaGetLastError();
+}
+
 cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((n + 255) / 256);

@@ -40,6 +40,8 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
     for dw in range(2 * r, max_dw + 1, 2 * r):
         xt = one_warp_xtile(dw, r, v)
         xts = {xt, max(v, (xt // 2) // v * v)}
+        ntile = -(-s.nx // xt)  # the same number of x tiles, evenly wide
+        xts.add(max(v, -(-(-(-s.nx // ntile)) // v) * v))
         for nclu in (2, 4, 8):  # x tiles splitting the row into portable cluster sizes
             xts.add(max(v, ((s.nx + nclu - 1) // nclu + v - 1) // v * v))
         for xtile in sorted(xts, reverse=True):

@@ -397,15 +397,14 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
     void* lam[2] = {ws + (size_t)(nck + k) * fb, ws + (size_t)(nck + k + 1) * fb};
     SweepArgs a = args_of(h);
     cudaStream_t s = h->stream;
-    cudaError_t e;
     double* gC[13] = {};
     for (int m = 0; m < nc; ++m) {
         gC[m] = static_cast<double*>(g_coef[m]);
-        if ((e = fill_value(gC[m], cnt, DT_F64, 0.0, s)) != cudaSuccess) return STENCIL_ECUDA;
+        if (fill_value(gC[m], cnt, DT_F64, 0.0, s) != cudaSuccess) return STENCIL_ECUDA;
         ++h->launches;
     }
-    if ((e = fill_value(lam[1], cnt, h->fdt, 0.0, s)) != cudaSuccess) return STENCIL_ECUDA;
-    if ((e = copy_interior_zero_halo(h->L, h->fdt, lambda_T, lam[0], s)) != cudaSuccess) return STENCIL_ECUDA;
+    if (fill_value(lam[1], cnt, h->fdt, 0.0, s) != cudaSuccess) return STENCIL_ECUDA;
+    if (copy_interior_zero_halo(h->L, h->fdt, lambda_T, lam[0], s) != cudaSuccess) return STENCIL_ECUDA;
     h->launches += 2;
     // in-segment states inherit the Dirichlet halo of u_0
     for (int j = 1; j < k; ++j)
@@ -416,11 +415,11 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
         const int t1 = (t0 + k < T) ? t0 + k : T;
         auto st = [&](int j) { return j == 0 ? ckpt(c) : state(j); };
         for (int j = 1; j < t1 - t0; ++j) {
-            if ((e = plain_step(a, st(j - 1), st(j), s)) != cudaSuccess) return STENCIL_ECUDA;
+            if (plain_step(a, st(j - 1), st(j), s) != cudaSuccess) return STENCIL_ECUDA;
             ++h->launches;
         }
         for (int t = t1 - 1; t >= t0; --t) {
-            if ((e = adjoint_step(a, lam[cur], st(t - t0), lam[cur ^ 1], gC, true, s)) != cudaSuccess)
+            if (adjoint_step(a, lam[cur], st(t - t0), lam[cur ^ 1], gC, true, s) != cudaSuccess)
                 return STENCIL_ECUDA;
             ++h->launches;
             cur ^= 1;

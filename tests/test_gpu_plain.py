@@ -79,3 +79,35 @@ def test_constant_invariant_bitwise(fdt):
         s.set_field(torch.full((19, 23, 37), 0.75, dtype=tdt), halo=0.75)
         s.run(5)
         assert torch.all(s.get_field() == 0.75)
+
+
+@pytest.mark.parametrize("shape", [(37, 29, 21), (64, 16, 8), (5, 3, 2)])
+@pytest.mark.parametrize("fdt", ["f32", "f64"])
+def test_set_and_get_field_through_every_memory_kind(shape, fdt):
+    """set_field / get_field with device memory, page-locked host memory (moved by the
+    library's copy kernel over the host link) and pageable host memory (pitched DMA): the
+    same interior, bit for bit, the halo left at the Dirichlet value; row lengths that are and
+    are not a multiple of 16 bytes."""
+    import torch
+    p = Problem("7pt_var", *shape, fdt=fdt, seed=31, halo=0.75)
+    tdt = torch.float32 if fdt == "f32" else torch.float64
+    ref = torch.from_numpy(p.u0).to(tdt)
+    sources = {"device": ref.cuda(), "pinned": ref.clone().pin_memory(), "pageable": ref.clone()}
+    for name, src in sources.items():
+        s = p.make()
+        s.set_field(src, halo=0.75)
+        torch.cuda.synchronize()
+        dense = s.get_field().cpu()
+        assert torch.equal(dense, ref), name
+        padded = s.padded(s.fields[s.parity]).cpu()
+        lay = s.layout
+        r, xo = lay.radius, lay.x_offset
+        inner = torch.zeros_like(padded, dtype=torch.bool)
+        inner[r:r + s.nz, r:r + s.ny, xo:xo + s.nx] = True
+        halo = padded[~inner]
+        assert torch.all(halo == 0.75), name
+        for oname, out in {"device": torch.empty_like(ref, device="cuda"),
+                           "pinned": torch.empty_like(ref).pin_memory(), "pageable": torch.empty_like(ref)}.items():
+            s.get_field(out)
+            torch.cuda.synchronize()
+            assert torch.equal(out.cpu(), ref), (name, oname)

@@ -47,15 +47,48 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--case", default=None,
                     help="profiling helper: KIND:N:FIELD:COEF:SCHEME:T[:dw,nf,warps,xtile] runs that "
-                         "case twice and exits (no JSON)")
+                         "case twice and exits (no JSON); also adjoint:KIND:N:FIELD:T and "
+                         "batch[:dw,nf,warps]")
     return ap.parse_args()
 
 
 def run_case(spec: str, seed: int):
-    """Set up one grid and run it twice (used for ncu captures of single kernels)."""
+    """Set up one grid and run it twice (used for ncu captures of single kernels).
+    Also: adjoint:KIND:N:FIELD:T (forward with checkpoints + adjoint through autograd, twice)
+    and batch[:dw,nf,warps] (the 64-grid 7-point variable FP32 batch, launched twice)."""
     import torch
     from paper_1410_5561_gb300.stencil import Tuning
     parts = spec.split(":")
+    dev = torch.device("cuda", 0)
+    if parts[0] == "adjoint":
+        from paper_1410_5561_gb300 import inputs
+        from paper_1410_5561_gb300.autograd import sweep
+        kind, n, fdt, T = parts[1], int(parts[2]), parts[3], int(parts[4])
+        s, u0 = make_grid(kind, n, fdt, None, seed, dev)
+        coefs = torch.stack([s.interior_of(c).clone() for c in s.coefs])
+        target = torch.empty_like(u0)
+        inputs.fill_uniform_torch(target, seed, inputs.STREAM_TARGET, -1.0, 1.0)
+        for _ in range(2):
+            u = u0.clone().requires_grad_(True)
+            c = coefs.clone().requires_grad_(True)
+            (0.5 * ((sweep(u, c, s, T) - target) ** 2).sum()).backward()
+        torch.cuda.synchronize(dev)
+        print("case done", spec, flush=True)
+        return 0
+    if parts[0] == "batch":
+        from paper_1410_5561_gb300 import inputs
+        from paper_1410_5561_gb300.batch import Batch
+        tn = Tuning(*[int(v) for v in parts[1].split(",")], 0) if len(parts) > 1 else Tuning(4, 1, 8, 0)
+        shapes = inputs.batch_shapes(seed)
+        grids = [make_grid_shape("7pt_var", nx, ny, nz, "f32", None, seed + q, dev)[0]
+                 for q, (nx, ny, nz, T) in enumerate(shapes)]
+        b = Batch(grids, [sh[3] for sh in shapes], tn)
+        for _ in range(2):
+            b.launch()
+        torch.cuda.synchronize(dev)
+        assert b.status() == 0
+        print("case done", spec, flush=True)
+        return 0
     kind, n, fdt, cdt, scheme, T = parts[0], int(parts[1]), parts[2], parts[3], parts[4], int(parts[5])
     tn = Tuning(*[int(v) for v in parts[6].split(",")]) if len(parts) > 6 else None
     s, _ = make_grid(kind, n, fdt, None if cdt in ("", "-") else cdt, seed, torch.device("cuda", 0))

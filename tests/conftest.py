@@ -25,3 +25,20 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _libraries_built(request):
+    """GPU sessions build the CUDA library and the oracle first if they are missing or stale
+    (an up-to-date build is a no-op)."""
+    try:
+        import torch
+        have_gpu = torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        have_gpu = False
+    if have_gpu and any("gpu" in it.keywords for it in request.session.items):
+        from paper_1410_5561_gb300 import build
+        build.build()
+        import oracle
+        oracle.build()
+    yield

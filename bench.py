@@ -236,33 +236,21 @@ def make_grid(kind, n, fdt, cdt, seed, device):
 
 
 def make_grid_shape(kind, nx, ny, nz, fdt, cdt, seed, device):
-    """A Stencil with seeded inputs generated on the device (same values as the CPU recipe's
-    draws; coefficients normalised as in paper_1410_5561_gb300.inputs)."""
+    """A Stencil with seeded inputs generated on the device (the same values as the CPU
+    recipe in paper_1410_5561_gb300.inputs, rounded once to the grid's precisions)."""
     import torch
     from paper_1410_5561_gb300 import inputs
     from paper_1410_5561_gb300.stencil import Stencil
     tdt = {"f32": torch.float32, "f64": torch.float64}[fdt]
     tcd = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[cdt or fdt]
     s = Stencil(kind, nx, ny, nz, dtype=tdt, coef_dtype=tcd, device=device)
-    u0 = torch.empty((nz, ny, nx), dtype=tdt, device=device)
-    inputs.fill_uniform_torch(u0, seed, inputs.STREAM_U0, -1.0, 1.0)
+    u0 = inputs.field_u0_torch(seed, nx, ny, nz, tdt, device)
     if kind == "7pt_const":
         s.set_coeffs(scalars=(0.4, 0.1))
     else:
-        nc = 7 if kind == "7pt_var" else 13
-        acc = None
-        rs = []
-        for m in range(nc):
-            r = torch.empty((nz, ny, nx), dtype=torch.float64, device=device)
-            inputs.fill_uniform_torch(r, seed, inputs.STREAM_COEF0 + m, 0.0, 1.0)
-            w = r if (kind == "7pt_var" or m == 0) else 2.0 * r
-            acc = w.clone() if acc is None else acc.add_(w)
-            rs.append(r)
-        for m in range(nc):
-            rs[m] = (0.95 * rs[m] / acc).to(tcd)
-        del acc
-        s.set_coeffs(arrays=rs)
-        del rs
+        cs = inputs.coefs_torch(kind, seed, nx, ny, nz, tcd, device)
+        s.set_coeffs(arrays=cs)
+        del cs
     s.set_field(u0, halo=0.0)
     torch.cuda.synchronize(device)
     return s, u0

@@ -132,14 +132,35 @@ def field_target(seed: int, nx: int, ny: int, nz: int, dtype=np.float64) -> np.n
     return uniform(seed, STREAM_TARGET, (nz, ny, nx), -1.0, 1.0, dtype)
 
 
+def _normalise(kind: str, r, row_sum: float):
+    """Coefficient arrays from raw draws r[m] (numpy or torch FP64, any shape).
+
+    7-point: C_m = row_sum * r_m / (r_0 + ... + r_6), so the seven weights of a
+    point sum to row_sum. 25-point: C_m = row_sum * r_m / (r_0 + 2 (r_1 + ... + r_12)),
+    since C_1..C_12 each weigh two neighbours. The sums run left to right and the
+    same operations are done on either array type, so host and device values agree
+    bit for bit.
+    """
+    if kind == "7pt_var":
+        s = r[0] + r[1]
+        for m in range(2, 7):
+            s = s + r[m]
+    else:
+        t = r[1] + r[2]
+        for m in range(3, 13):
+            t = t + r[m]
+        s = r[0] + 2.0 * t
+    return [row_sum * r[m] / s for m in range(len(r))]
+
+
 def coefs_7pt_var(seed: int, nx: int, ny: int, nz: int, row_sum: float = 0.95) -> np.ndarray:
     """Seven coefficient arrays (C0..C6), shape (7, nz, ny, nx), FP64.
 
     Order and neighbour of each array follow Listing 2: C0 centre, C1 +x,
     C2 -x, C3 +y, C4 -y, C5 +z, C6 -z.
     """
-    r = np.stack([uniform(seed, STREAM_COEF0 + m, (nz, ny, nx)) for m in range(7)])
-    return row_sum * r / r.sum(axis=0, keepdims=True)
+    r = [uniform(seed, STREAM_COEF0 + m, (nz, ny, nx)) for m in range(7)]
+    return np.stack(_normalise("7pt_var", r, row_sum))
 
 
 def coefs_25pt_var(seed: int, nx: int, ny: int, nz: int, row_sum: float = 0.95) -> np.ndarray:
@@ -148,9 +169,57 @@ def coefs_25pt_var(seed: int, nx: int, ny: int, nz: int, row_sum: float = 0.95) 
     C00 weighs the centre; C(3(d-1)+a+1) weighs the pair at distance d on axis
     a (x=0, y=1, z=2), as in Listing 3.
     """
-    r = np.stack([uniform(seed, STREAM_COEF0 + m, (nz, ny, nx)) for m in range(13)])
-    s = r[0] + 2.0 * r[1:].sum(axis=0)
-    return row_sum * r / s[None]
+    r = [uniform(seed, STREAM_COEF0 + m, (nz, ny, nx)) for m in range(13)]
+    return np.stack(_normalise("25pt_var", r, row_sum))
+
+
+def box_uniform(seed: int, stream: int, shape, lo, hi, a: float = 0.0, b: float = 1.0) -> np.ndarray:
+    """The values of ``uniform(seed, stream, shape, a, b)`` inside the box [lo, hi) (index
+    order (z, y, x)), drawn without materialising the whole array."""
+    nz, ny, nx = shape
+    k = np.arange(lo[0], hi[0], dtype=np.uint64)[:, None, None]
+    j = np.arange(lo[1], hi[1], dtype=np.uint64)[None, :, None]
+    i = np.arange(lo[2], hi[2], dtype=np.uint64)[None, None, :]
+    n = (k * np.uint64(ny) + j) * np.uint64(nx) + i + np.uint64(1)  # counter of flat index
+    key = stream_key(seed, stream)
+    with np.errstate(over="ignore"):
+        x = _mix_np(key + n * _G)
+    return a + (b - a) * ((x >> np.uint64(11)).astype(np.float64) * (2.0 ** -53))
+
+
+def field_u0_box(seed: int, nx: int, ny: int, nz: int, lo, hi) -> np.ndarray:
+    """``field_u0(seed, nx, ny, nz)[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]``."""
+    return box_uniform(seed, STREAM_U0, (nz, ny, nx), lo, hi, -1.0, 1.0)
+
+
+def coefs_box(kind: str, seed: int, nx: int, ny: int, nz: int, lo, hi, row_sum: float = 0.95) -> np.ndarray:
+    """The coefficient arrays of ``coefs_7pt_var`` / ``coefs_25pt_var`` inside a box."""
+    nc = 7 if kind == "7pt_var" else 13
+    r = [box_uniform(seed, STREAM_COEF0 + m, (nz, ny, nx), lo, hi) for m in range(nc)]
+    return np.stack(_normalise(kind, r, row_sum))
+
+
+def field_u0_torch(seed: int, nx: int, ny: int, nz: int, dtype, device):
+    """``field_u0`` drawn on a torch device, rounded once to ``dtype``."""
+    import torch
+    out = torch.empty((nz, ny, nx), dtype=dtype, device=device)
+    return fill_uniform_torch(out, seed, STREAM_U0, -1.0, 1.0)
+
+
+def coefs_torch(kind: str, seed: int, nx: int, ny: int, nz: int, dtype, device, row_sum: float = 0.95):
+    """The coefficient arrays of ``coefs_7pt_var`` / ``coefs_25pt_var`` computed on a torch
+    device in FP64 and rounded once to ``dtype``; a list of (nz, ny, nx) tensors."""
+    import torch
+    nc = 7 if kind == "7pt_var" else 13
+    r = []
+    for m in range(nc):
+        t = torch.empty((nz, ny, nx), dtype=torch.float64, device=device)
+        r.append(fill_uniform_torch(t, seed, STREAM_COEF0 + m, 0.0, 1.0))
+    c = _normalise(kind, r, row_sum)
+    del r
+    if dtype == torch.bfloat16:  # bf16_bits' rounding: to FP32 first, then to bfloat16
+        return [x.to(torch.float32).to(dtype) for x in c]
+    return [x.to(dtype) for x in c]
 
 
 def batch_shapes(seed: int, count: int = 64, side_lo: int = 32, side_hi: int = 192,

@@ -191,6 +191,14 @@ class Stencil:
         r, xo = lay.radius, lay.x_offset
         return t.view(lay.planes, lay.pitch_y, lay.pitch_x)[r:r + self.nz, r:r + self.ny, xo:xo + self.nx]
 
+    def coef_interior(self, m: int) -> torch.Tensor:
+        """Interior view (no copy) of coefficient array m, in the coefficient layout (whose
+        pitch differs from the field's when the coefficients are stored in BF16)."""
+        cl = self._layout(C.STENCIL_COEF_ARRAY)
+        r, xo = cl.radius, cl.x_offset
+        v = self.coefs[m].view(cl.planes, cl.pitch_y, cl.pitch_x)
+        return v[r:r + self.nz, r:r + self.ny, xo:xo + self.nx]
+
     @property
     def launches(self) -> int:
         """Kernels this grid has launched so far."""

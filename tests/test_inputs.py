@@ -78,3 +78,28 @@ def test_torch_generator_matches_numpy():
     g = np.empty((5, 5, 5), dtype=np.float32)
     inputs.fill_uniform(g, 0, 0, -1.0, 1.0)
     assert np.array_equal(f.numpy(), g)
+
+
+def test_box_and_device_recipes_equal_the_full_arrays():
+    """Crops drawn on their own, and the torch versions of the recipes, give exactly the
+    values of the full CPU arrays: full-size parity cases build the device grid with the
+    torch recipe and hand the oracle a crop."""
+    torch = __import__("pytest").importorskip("torch")
+    nx, ny, nz, seed = 11, 9, 7, 4
+    lo, hi = (2, 1, 3), (6, 9, 10)
+    sl = np.s_[lo[0]:hi[0], lo[1]:hi[1], lo[2]:hi[2]]
+    assert np.array_equal(inputs.field_u0_box(seed, nx, ny, nz, lo, hi), inputs.field_u0(seed, nx, ny, nz)[sl])
+    u = inputs.field_u0_torch(seed, nx, ny, nz, torch.float32, "cpu")
+    assert np.array_equal(u.numpy(), inputs.field_u0(seed, nx, ny, nz).astype(np.float32))
+    for kind, full in (("7pt_var", inputs.coefs_7pt_var), ("25pt_var", inputs.coefs_25pt_var)):
+        c = full(seed, nx, ny, nz)
+        assert np.array_equal(inputs.coefs_box(kind, seed, nx, ny, nz, lo, hi), c[(slice(None),) + sl])
+        d = inputs.coefs_torch(kind, seed, nx, ny, nz, torch.float64, "cpu")
+        assert np.array_equal(np.stack([x.numpy() for x in d]), c)
+        b = inputs.coefs_torch(kind, seed, nx, ny, nz, torch.bfloat16, "cpu")
+        bits = np.stack([x.view(torch.int16).numpy().view(np.uint16) for x in b])
+        assert np.array_equal(bits, inputs.bf16_bits(c))
+    full_x = (0, 2, 0), (4, 7, nx)
+    c = inputs.coefs_25pt_var(seed, nx, ny, nz)
+    got = inputs.coefs_box("25pt_var", seed, nx, ny, nz, *full_x)
+    assert np.array_equal(got, c[:, 0:4, 2:7, :])

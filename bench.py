@@ -93,10 +93,16 @@ def run_case(spec: str, seed: int):
     tn = Tuning(*[int(v) for v in parts[6].split(",")]) if len(parts) > 6 else None
     s, _ = make_grid(kind, n, fdt, None if cdt in ("", "-") else cdt, seed, torch.device("cuda", 0))
     s.set_tuning(scheme, tn)
-    for _ in range(2):
-        s.run(T)
-        s.sync()
-    print("case done", spec, flush=True)
+    s.run(T)
+    s.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.run(T)
+    e1.record(s.stream)
+    e1.synchronize()
+    sec = e0.elapsed_time(e1) / 1e3
+    print(f"case done {spec} {1e3 * sec:.3f} ms {float(n) ** 3 * T / sec / 1e9:.1f} GLUP/s", flush=True)
     return 0
 
 
@@ -495,6 +501,7 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_oracle_sample()
         if not args.no_extras:
             for key, fn in (("per_stencil", lambda: per_stencil(device, args.seed, hbm_peak, fp32_peak, fp64_peak)),
+                            ("dw_sweep", lambda: dw_sweep(device, args.seed)),
                             ("batched", lambda: batched(device, args.seed)),
                             ("adjoint", lambda: adjoint_timing(device, args.seed))):
                 try:
@@ -550,6 +557,44 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
         del s, u0
         torch.cuda.empty_cache()
     return rows
+
+
+DW_SWEEP = ("7pt_const", 512, "f32", None, 100)
+
+
+def dw_sweep(device, seed, per_dw: int = 2):
+    """Blocked GLUP/s at each feasible diamond width D_w (7-point constant FP32 512^3, T=100):
+    the best of the first ``per_dw`` tuner candidates with that D_w, beside the Eq. 5 model code
+    balance 2R(4 s_f)/D_w and the plain sweep."""
+    import torch
+    from paper_1410_5561_gb300 import model, tuner
+    kind, n, fdt, cdt, T = DW_SWEEP
+    s, _ = make_grid(kind, n, fdt, cdt, seed, device)
+    lups = float(n) ** 3 * T
+    s.set_tuning("plain")
+    out = {"stencil": kind, "grid": n, "field": fdt, "T": T,
+           "plain_glups": lups / (timed(s, T, 2, 1) / 2) / 1e9,
+           "plain_model_bytes_per_lup": model.bytes_per_lup(kind, fdt, cdt, "plain"), "rows": []}
+    cands = tuner.candidates(s)
+    for dw in sorted({t.dw for t in cands}):
+        best = None
+        for tn in [t for t in cands if t.dw == dw][:per_dw]:
+            try:
+                s.set_tuning("blocked", tn)
+            except Exception:
+                continue
+            sec = timed(s, T, 2, 1) / 2
+            if best is None or sec < best[0]:
+                best = (sec, tn)
+        if best is None:
+            continue
+        sec, tn = best
+        out["rows"].append({"dw": dw, "tuning": {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile},
+                            "glups": lups / sec / 1e9,
+                            "model_bytes_per_lup": model.bytes_per_lup(kind, fdt, cdt, "blocked", dw)})
+    del s
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched(device, seed):

@@ -50,7 +50,17 @@ typedef struct stencil_grid* stencil_t; /* opaque, owned by the library */
 enum stencil_kind { STENCIL_7PT_CONST = 0, STENCIL_7PT_VAR = 1, STENCIL_25PT_VAR = 2 };
 enum stencil_dtype { STENCIL_F32 = 0, STENCIL_F64 = 1, STENCIL_BF16 = 2 };
 enum stencil_scheme { STENCIL_PLAIN = 0, STENCIL_BLOCKED = 1, STENCIL_AUTO = 2 };
-enum stencil_where { STENCIL_HOST = 0, STENCIL_DEVICE = 1 };
+/* Where a dense array passed to set_coeffs / set_field / get_field lives.
+ * STENCIL_HOST: host memory; the call waits for its copy when the caller needs
+ * the data back (page-locked memory is moved by the library's copy kernel,
+ * pageable memory by a pitched DMA). STENCIL_DEVICE: device memory.
+ * STENCIL_HOST_ASYNC (set_field / get_field only): page-locked host memory,
+ * moved by the copy engines (a pitched DMA) on the handle's stream without
+ * waiting and without occupying SMs, so that the transfer can overlap a sweep
+ * running on another stream; the caller keeps the host array alive and
+ * unchanged (set_field) or unread (get_field) until the stream has passed the
+ * copy. Pageable memory is rejected with STENCIL_EINVAL. */
+enum stencil_where { STENCIL_HOST = 0, STENCIL_DEVICE = 1, STENCIL_HOST_ASYNC = 2 };
 enum stencil_array { STENCIL_FIELD_ARRAY = 0, STENCIL_COEF_ARRAY = 1, STENCIL_GRAD_ARRAY = 2 };
 
 enum stencil_status {
@@ -119,8 +129,9 @@ int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* ar
 
 /* Initial field u_0: dense interior src (field dtype, host or device). Both
  * field arrays get every non-interior cell set to halo_value (the Dirichlet
- * value, never written again by a sweep); src goes to the interior of field_a,
- * which becomes the current array (time 0). */
+ * value, never written again by a sweep: the fill is skipped when the bound
+ * arrays already hold this value there from an earlier set_field); src goes to
+ * the interior of field_a, which becomes the current array (time 0). */
 int stencil_set_field(stencil_t h, const void* src, double halo_value, int where);
 
 /* Select the schedule used by run(): STENCIL_PLAIN (one launch per step),
@@ -262,6 +273,11 @@ int stencil_batch_destroy(stencil_batch_t b);
  * before the previous one has finished on another stream) race on it. */
 int stencil_batch_run_noalloc(const stencil_t* grids, const int* T, int n, const stencil_tuning* tuning,
                               void* cuda_stream, int* status_out);
+
+/* Make the handle's later calls enqueue their work on cuda_stream (NULL: the
+ * legacy default stream). Ordering against work already enqueued on the
+ * previous stream is the caller's (events). */
+int stencil_set_stream(stencil_t h, void* cuda_stream);
 
 /* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error. */
 int stencil_sync(stencil_t h);

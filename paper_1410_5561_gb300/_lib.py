@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(HERE, "libstencil_gb300.so")
 STENCIL_7PT_CONST, STENCIL_7PT_VAR, STENCIL_25PT_VAR = 0, 1, 2
 STENCIL_F32, STENCIL_F64, STENCIL_BF16 = 0, 1, 2
 STENCIL_PLAIN, STENCIL_BLOCKED, STENCIL_AUTO = 0, 1, 2
-STENCIL_HOST, STENCIL_DEVICE = 0, 1
+STENCIL_HOST, STENCIL_DEVICE, STENCIL_HOST_ASYNC = 0, 1, 2
 STENCIL_FIELD_ARRAY, STENCIL_COEF_ARRAY, STENCIL_GRAD_ARRAY = 0, 1, 2
 
 STATUS = {0: "STENCIL_OK", -1: "STENCIL_EINVAL", -2: "STENCIL_ENOSMEM", -3: "STENCIL_ETIMEOUT",
@@ -79,6 +79,7 @@ SIGNATURES = [
     ("stencil_batch_destroy", _I, [_H]),
     ("stencil_batch_run_noalloc", _I, [ctypes.POINTER(_H), ctypes.POINTER(_I), _I, ctypes.POINTER(stencil_tuning),
                                        _P, ctypes.POINTER(_I)]),
+    ("stencil_set_stream", _I, [_H, _P]),
     ("stencil_sync", _I, [_H]),
     ("stencil_strerror", ctypes.c_char_p, [_I]),
     ("stencil_destroy", _I, [_H]),

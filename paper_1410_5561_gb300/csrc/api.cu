@@ -27,6 +27,7 @@ struct stencil_grid {
     bool tune_set;
     long long launches;
     long long plan_key;  // persistent blocked plan currently in the workspace (-1: none)
+    bool halo_ok;        // both bound field arrays hold `halo` in every non-interior cell
 };
 
 static int from_cuda(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
@@ -145,6 +146,7 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
     h->tune_set = false;
     h->launches = 0;
     h->plan_key = -1;
+    h->halo_ok = false;
     *out = h;
     return STENCIL_OK;
 }
@@ -183,16 +185,24 @@ int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, v
     if (workspace && !aligned16(workspace)) return STENCIL_EINVAL;
     h->ws = workspace;
     h->plan_key = -1;
+    h->halo_ok = false;
     h->bound = true;
     return STENCIL_OK;
 }
 
-static cudaError_t copy_interior(const stencil_grid* h, int eb, const void* dense, void* padded, bool to_padded) {
+static cudaError_t copy_interior(const stencil_grid* h, int eb, const void* dense, void* padded, bool to_padded,
+                                 bool dma = false) {
     const Layout& L = h->L;
     // device memory, or page-locked host memory the device can address: the library's copy
-    // kernel; pageable host memory: a pitched DMA
+    // kernel; pageable host memory, or dma: a pitched DMA
     cudaPointerAttributes at{};
-    if (cudaPointerGetAttributes(&at, dense) == cudaSuccess) {
+    if (dma) {
+        if (cudaPointerGetAttributes(&at, dense) != cudaSuccess) {
+            cudaGetLastError();
+            return cudaErrorInvalidValue;
+        }
+        if (at.type != cudaMemoryTypeHost) return cudaErrorInvalidValue;
+    } else if (cudaPointerGetAttributes(&at, dense) == cudaSuccess) {
         const void* dp = nullptr;
         if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) dp = dense;
         else if (at.type == cudaMemoryTypeHost) dp = at.devicePointer;
@@ -247,16 +257,24 @@ int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* ar
 
 int stencil_set_field(stencil_t h, const void* src, double halo_value, int where) {
     if (!h || !src) return STENCIL_EINVAL;
-    if (where != STENCIL_HOST && where != STENCIL_DEVICE) return STENCIL_EINVAL;
+    if (where != STENCIL_HOST && where != STENCIL_DEVICE && where != STENCIL_HOST_ASYNC) return STENCIL_EINVAL;
     if (!h->bound) return STENCIL_EUNBOUND;
-    for (int i = 0; i < 2; ++i) {
-        cudaError_t e = fill_value(h->field[i], h->L.count(), h->fdt, halo_value, h->stream);
-        if (e != cudaSuccess) return STENCIL_ECUDA;
-        ++h->launches;
+    // sweeps write interior cells only, so a halo set by an earlier call on the same arrays
+    // stays (the interior of the second array is written before it is read)
+    const bool same = h->halo_ok && memcmp(&h->halo, &halo_value, sizeof(double)) == 0;
+    if (!same) {
+        h->halo_ok = false;
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = fill_value(h->field[i], h->L.count(), h->fdt, halo_value, h->stream);
+            if (e != cudaSuccess) return STENCIL_ECUDA;
+            ++h->launches;
+        }
     }
-    cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), src, h->field[0], true);
+    cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), src, h->field[0], true, where == STENCIL_HOST_ASYNC);
+    if (e == cudaErrorInvalidValue && where == STENCIL_HOST_ASYNC) return STENCIL_EINVAL;
     if (e != cudaSuccess) return STENCIL_ECUDA;
     h->halo = halo_value;
+    h->halo_ok = true;
     h->parity = 0;
     return STENCIL_OK;
 }
@@ -333,9 +351,10 @@ int stencil_parity(stencil_t h) { return h ? h->parity : STENCIL_EINVAL; }
 
 int stencil_get_field(stencil_t h, void* dst, int where) {
     if (!h || !dst) return STENCIL_EINVAL;
-    if (where != STENCIL_HOST && where != STENCIL_DEVICE) return STENCIL_EINVAL;
+    if (where != STENCIL_HOST && where != STENCIL_DEVICE && where != STENCIL_HOST_ASYNC) return STENCIL_EINVAL;
     if (!h->bound) return STENCIL_EUNBOUND;
-    cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), dst, h->field[h->parity], false);
+    cudaError_t e = copy_interior(h, dtype_bytes(h->fdt), dst, h->field[h->parity], false, where == STENCIL_HOST_ASYNC);
+    if (e == cudaErrorInvalidValue && where == STENCIL_HOST_ASYNC) return STENCIL_EINVAL;
     if (e != cudaSuccess) return STENCIL_ECUDA;
     if (where == STENCIL_HOST) return from_cuda(cudaStreamSynchronize(h->stream));
     return STENCIL_OK;
@@ -557,6 +576,12 @@ int stencil_batch_inject_stall(stencil_batch_t b, int item) {
 int stencil_batch_destroy(stencil_batch_t b) {
     if (!b) return STENCIL_EINVAL;
     delete b;
+    return STENCIL_OK;
+}
+
+int stencil_set_stream(stencil_t h, void* cuda_stream) {
+    if (!h) return STENCIL_EINVAL;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
     return STENCIL_OK;
 }
 

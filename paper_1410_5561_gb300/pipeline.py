@@ -1,0 +1,82 @@
+"""Independent problems streamed through one grid with host transfers overlapping the sweeps.
+
+Each job is one initial field on the host, advanced by T steps, with u_T read back to the
+host. The host link is far slower than HBM (about 200 GB/s per direction against 6.8 TB/s),
+so moving a 1024^3 FP32 field in and out costs close to a third of a 100-step sweep when
+the phases run one after another. Here the copy engines move dense fields between the host
+and two dense device staging arrays on their own streams, while the sweep of the previous
+job runs; the grid's own kernels scatter the staged field into the padded layout before a
+sweep and gather u_T out of it afterwards (a device-to-device pass of a few milliseconds).
+Per job, ordered by events:
+
+    h2d(i):     host input i -> staging_in       after load(i - 1) has read staging_in
+    compute(i): load(i) = set_field(staging_in); run(T);
+                store(i) = get_field(staging_out) after d2h(i - 1) has emptied staging_out
+    d2h(i):     staging_out -> host output i     after store(i)
+
+so the compute stream holds only the sweeps and the two short device passes, and the link
+transfers of jobs i + 1 and i - 1 proceed beside the sweep of job i. Results are identical
+to running the jobs one by one (the same kernels on the same values).
+"""
+from __future__ import annotations
+
+import torch
+
+from .stencil import Stencil
+
+
+class Pipeline:
+    def __init__(self, grid: Stencil, T: int, halo: float = 0.0):
+        self.grid = grid
+        self.T = int(T)
+        self.halo = float(halo)
+        dev = grid.device
+        shape = (grid.nz, grid.ny, grid.nx)
+        self.staging_in = torch.empty(shape, dtype=grid.dtype, device=dev)
+        self.staging_out = torch.empty(shape, dtype=grid.dtype, device=dev)
+        self.compute = torch.cuda.Stream(dev)
+        self.h2d = torch.cuda.Stream(dev)
+        self.d2h = torch.cuda.Stream(dev)
+
+    def run(self, inputs: list[torch.Tensor], outputs: list[torch.Tensor]) -> torch.cuda.Event:
+        """Advance every ``inputs[i]`` (page-locked host, (nz, ny, nx)) by T steps into
+        ``outputs[i]`` (page-locked host; a buffer listed twice ends up holding the later job's
+        result). Returns the event recorded after the last copy out; the outputs are valid once
+        it has completed."""
+        if len(inputs) != len(outputs):
+            raise ValueError("one output per input")
+        g = self.grid
+        for t in list(inputs) + list(outputs):
+            if t.device.type != "cpu" or not t.is_pinned() or t.dtype != g.dtype or not t.is_contiguous():
+                raise ValueError("inputs and outputs must be contiguous page-locked host tensors of the "
+                                 "grid's dtype")
+        saved = g.stream
+        cur = torch.cuda.current_stream(g.device)
+        start = cur.record_event()
+        for st in (self.h2d, self.compute, self.d2h):
+            st.wait_event(start)
+        consumed = emptied = last = None
+        g.set_stream(self.compute)
+        for src, dst in zip(inputs, outputs):
+            with torch.cuda.stream(self.h2d):
+                if consumed is not None:
+                    self.h2d.wait_event(consumed)
+                self.staging_in.copy_(src, non_blocking=True)
+                loaded = self.h2d.record_event()
+            self.compute.wait_event(loaded)
+            g.set_field(self.staging_in, halo=self.halo)
+            consumed = self.compute.record_event()
+            g.run(self.T)
+            if emptied is not None:
+                self.compute.wait_event(emptied)
+            g.get_field(self.staging_out)
+            ready = self.compute.record_event()
+            with torch.cuda.stream(self.d2h):
+                self.d2h.wait_event(ready)
+                dst.copy_(self.staging_out, non_blocking=True)
+                emptied = last = self.d2h.record_event()
+        for st in (self.h2d, self.compute, self.d2h):
+            cur.wait_stream(st)
+        g.set_stream(saved)
+        saved.wait_stream(cur)
+        return last

@@ -126,23 +126,46 @@ class Stencil:
             self.sync()
         self._keep = arrs  # device sources stay alive until the copies are done
 
-    def set_field(self, u0: torch.Tensor, halo: float = 0.0):
+    def set_field(self, u0: torch.Tensor, halo: float = 0.0, async_host: bool = False):
+        """Initial field from a dense (nz, ny, nx) tensor on the host or the device.
+
+        ``async_host``: ``u0`` is page-locked host memory copied by the copy engines on this
+        grid's stream without waiting (STENCIL_HOST_ASYNC); the caller keeps it unchanged until
+        the stream has passed the copy."""
         u = u0.to(self.dtype).contiguous()
         assert tuple(u.shape) == (self.nz, self.ny, self.nx), u.shape
-        where = C.STENCIL_HOST if u.device.type == "cpu" else C.STENCIL_DEVICE
+        if async_host:
+            assert u.device.type == "cpu" and u.is_pinned() and u.data_ptr() == u0.data_ptr()
+            where = C.STENCIL_HOST_ASYNC
+        else:
+            where = C.STENCIL_HOST if u.device.type == "cpu" else C.STENCIL_DEVICE
         C.call("stencil_set_field", self._h, _ptr(u), float(halo), where)
         if where == C.STENCIL_HOST:
             self.sync()
         self._keep_u = u
 
-    def get_field(self, out: torch.Tensor | None = None) -> torch.Tensor:
-        """Dense interior copy of the current field (into ``out`` if given; host or device)."""
+    def get_field(self, out: torch.Tensor | None = None, async_host: bool = False) -> torch.Tensor:
+        """Dense interior copy of the current field (into ``out`` if given; host or device).
+
+        ``async_host``: ``out`` is page-locked host memory filled by the copy engines on this
+        grid's stream; the call returns at once and ``out`` is valid once the stream has passed
+        the copy (STENCIL_HOST_ASYNC)."""
         if out is None:
             out = torch.empty((self.nz, self.ny, self.nx), dtype=self.dtype, device=self.device)
         assert out.is_contiguous() and out.dtype == self.dtype
-        where = C.STENCIL_HOST if out.device.type == "cpu" else C.STENCIL_DEVICE
+        if async_host:
+            assert out.device.type == "cpu" and out.is_pinned()
+            where = C.STENCIL_HOST_ASYNC
+        else:
+            where = C.STENCIL_HOST if out.device.type == "cpu" else C.STENCIL_DEVICE
         C.call("stencil_get_field", self._h, _ptr(out), where)
         return out
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        """Enqueue this grid's later calls on ``stream`` (ordering with earlier work is the
+        caller's, through events)."""
+        C.call("stencil_set_stream", self._h, ctypes.c_void_p(stream.cuda_stream))
+        self.stream = stream
 
     # ------------------------------------------------------------ schedule
     def set_tuning(self, scheme: str = "plain", tuning: Tuning | None = None):

@@ -1,0 +1,105 @@
+"""Host transfers overlapped with sweeps: the staged pipeline, asynchronous copy-engine
+transfers, the stream switch and the halo kept between jobs, each against the plain
+one-job-at-a-time path (bit for bit: the same kernels on the same values)."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1410_5561_gb300 import _lib as C
+from paper_1410_5561_gb300.pipeline import Pipeline
+from paper_1410_5561_gb300.stencil import Tuning
+from tests._util import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+def _sequential(p, jobs, T, scheme, tn, halo):
+    s = p.make()
+    s.set_tuning(scheme, tn)
+    out = []
+    for u in jobs:
+        s.set_field(u, halo=halo)
+        s.run(T)
+        out.append(s.get_field().cpu())
+    return out
+
+
+@pytest.mark.parametrize("kind,shape,fdt,cdt,scheme,tn", [
+    ("7pt_const", (70, 33, 29), "f32", None, "blocked", Tuning(8, 2, 16, 56)),
+    ("7pt_var", (45, 26, 31), "f32", "bf16", "auto", None),
+    ("25pt_var", (29, 24, 22), "f64", None, "plain", None),
+])
+@pytest.mark.parametrize("T", [1, 8])
+def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T):
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=21, halo=0.25)
+    tdt = {"f32": torch.float32, "f64": torch.float64}[fdt]
+    g = torch.Generator().manual_seed(5)
+    jobs = [(torch.rand(shape[::-1], generator=g, dtype=torch.float64) * 2 - 1).to(tdt).pin_memory()
+            for _ in range(5)]
+    want = _sequential(p, jobs, T, scheme, tn, p.halo)
+    s = p.make()
+    s.set_tuning(scheme, tn)
+    outs = [torch.empty_like(u).pin_memory() for u in jobs]
+    pipe = Pipeline(s, T, halo=p.halo)
+    pipe.run(jobs, outs).synchronize()
+    for a, b in zip(outs, want):
+        assert torch.equal(a, b)
+    # a second pass through the same pipeline (halo kept, grid reused) gives the same
+    outs2 = [torch.empty_like(u).pin_memory() for u in jobs]
+    pipe.run(jobs[::-1], outs2).synchronize()
+    for a, b in zip(outs2, want[::-1]):
+        assert torch.equal(a, b)
+    # the grid is back on its own stream and usable one job at a time
+    s.set_field(jobs[0], halo=p.halo)
+    s.run(T)
+    assert torch.equal(s.get_field().cpu(), want[0])
+    with pytest.raises(ValueError):
+        pipe.run([jobs[0].clone()], [outs[0]])  # pageable input
+
+
+def test_async_host_transfers_and_halo_changes():
+    p = Problem("7pt_var", 40, 21, 17, fdt="f32", seed=22, halo=0.0)
+    s = p.make()
+    s.set_tuning("blocked", Tuning(8, 1, 8, 16))
+    u = torch.from_numpy(p.u0).float().pin_memory()
+    ref = {}
+    for halo in (0.0, 0.5):
+        q = Problem("7pt_var", 40, 21, 17, fdt="f32", seed=22, halo=halo)
+        ref[halo] = _sequential(q, [u], 6, "plain", None, halo)[0]
+    out = torch.empty_like(u).pin_memory()
+    # the halo follows each call's value; unchanged values keep the arrays' halo
+    for halo in (0.5, 0.5, 0.0, 0.0, 0.5):
+        s.set_field(u, halo=halo, async_host=True)
+        s.run(6)
+        s.get_field(out, async_host=True)
+        s.sync()
+        assert torch.equal(out, ref[halo]), halo
+    # a stream switch moves later work to the new stream
+    side = torch.cuda.Stream()
+    s.set_stream(side)
+    s.set_field(u, halo=0.0, async_host=True)
+    s.run(6)
+    s.get_field(out, async_host=True)
+    side.synchronize()
+    assert torch.equal(out, ref[0.0])
+
+
+def test_async_host_transfer_rejects_pageable_and_device_memory():
+    p = Problem("7pt_const", 12, 10, 8, fdt="f32", seed=23)
+    s = p.make()
+    pageable = torch.zeros((8, 10, 12), dtype=torch.float32)
+    dev = torch.zeros((8, 10, 12), dtype=torch.float32, device="cuda")
+    for t in (pageable, dev):
+        with pytest.raises(C.StencilError) as e:
+            C.call("stencil_set_field", s._h, ctypes.c_void_p(t.data_ptr()), 0.0, C.STENCIL_HOST_ASYNC)
+        assert e.value.status == -1
+        with pytest.raises(C.StencilError) as e:
+            C.call("stencil_get_field", s._h, ctypes.c_void_p(t.data_ptr()), C.STENCIL_HOST_ASYNC)
+        assert e.value.status == -1
+    # set_coeffs has no asynchronous form
+    c = (ctypes.c_double * 2)(0.4, 0.1)
+    with pytest.raises(C.StencilError):
+        C.call("stencil_set_coeffs", s._h, c, None, C.STENCIL_HOST_ASYNC)
+    assert np.isfinite(s.get_field().cpu().numpy()).all()

@@ -71,3 +71,14 @@ def test_host_only_entry_points(libpath):
     assert L.stencil_bind(h, ctypes.c_void_p(16), ctypes.c_void_p(16), None, None) == -1
     assert L.stencil_bind(h, ctypes.c_void_p(18), ctypes.c_void_p(32), None, None) == -1
     assert L.stencil_destroy(h) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the CUDA library every entry point raises; nothing falls back to the CPU."""
+    from paper_1410_5561_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "libstencil_gb300.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.lib()
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _lib.call("stencil_strerror", 0)

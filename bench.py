@@ -521,6 +521,7 @@ def run_ours(args):
         if not args.no_extras:
             for key, fn in (("per_stencil", lambda: per_stencil(device, args.seed, hbm_peak, fp32_peak, fp64_peak)),
                             ("dw_sweep", lambda: dw_sweep(device, args.seed)),
+                            ("energy", lambda: energy_table(device, args.seed)),
                             ("batched", lambda: batched(device, args.seed)),
                             ("adjoint", lambda: adjoint_timing(device, args.seed))):
                 try:
@@ -614,6 +615,61 @@ def dw_sweep(device, seed, per_dw: int = 2):
     del s
     torch.cuda.empty_cache()
     return out
+
+
+ENERGY_CASES = [
+    ("7pt_const", 1024, "f32", None, 100),
+    ("7pt_const", 512, "f32", None, 100),
+    ("7pt_var", 384, "f32", None, 50),
+    ("7pt_var", 384, "f32", "bf16", 50),
+]
+
+
+def energy_table(device, seed, min_seconds: float = 2.0):
+    """Board energy per LUP, plain vs blocked (the paper's Section IV question on the GPU):
+    NVML's total-energy counter read around at least ``min_seconds`` of back-to-back runs of
+    each schedule; the idle board power, read first over one second with nothing of ours
+    running, gives the dynamic share. Blocked runs use the tuning the benchmark's autotuner
+    chose for the grid (cached), else the tuner's first candidate."""
+    import torch
+    from paper_1410_5561_gb300 import energy, model, tuner
+    meter = energy.EnergyMeter(energy.device_uuid(device))
+    if not meter.available:
+        return {"unavailable": meter.reason}
+    torch.cuda.synchronize(device)
+    idle = energy.idle_watts(meter, 1.0)
+    rows = []
+    sync = lambda: torch.cuda.synchronize(device)  # noqa: E731
+    for kind, n, fdt, cdt, T in ENERGY_CASES:
+        s, _ = make_grid(kind, n, fdt, cdt, seed, device)
+        lups = float(n) ** 3 * T
+        row = {"stencil": kind, "grid": n, "field": fdt, "coef": cdt or fdt, "T": T}
+        for scheme in ("plain", "blocked"):
+            if scheme == "plain":
+                s.set_tuning("plain")
+                bpl = model.bytes_per_lup(kind, fdt, cdt, "plain")
+                tun = None
+            else:
+                tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+                bpl = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)
+                tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
+            s.run(T)
+            r = energy.measure(meter, lambda: s.run(T), lups, min_seconds=min_seconds, sync=sync)
+            if r is None:
+                row[scheme] = None
+                continue
+            dyn = None if idle is None else max(r["watts"] - idle, 0.0) * r["seconds"] / r["lups"] * 1e12
+            row[scheme] = {"pj_per_lup": r["pj_per_lup"], "dynamic_pj_per_lup": dyn, "watts": r["watts"],
+                           "glups": r["lups"] / r["seconds"] / 1e9, "model_bytes_per_lup": bpl,
+                           "tuning": tun}
+        if row.get("plain") and row.get("blocked"):
+            row["blocked_over_plain_energy"] = row["blocked"]["pj_per_lup"] / row["plain"]["pj_per_lup"]
+        rows.append(row)
+        del s
+        torch.cuda.empty_cache()
+    meter.close()
+    return {"idle_watts": idle, "counter": "nvmlDeviceGetTotalEnergyConsumption (whole board)",
+            "rows": rows}
 
 
 def batched(device, seed):

@@ -456,12 +456,14 @@ def run_ours(args):
         pipe = Pipeline(s, T, halo=0.0)
         pipe.run([host_in] * 2, host_out).synchronize()  # warm-up
         kp = max(3, args.steps)  # jobs in flight amortise the first copy in and the last copy out
-        barrier()
-        t0 = time.perf_counter()
-        pipe.run([host_in] * kp, [host_out[i % 2] for i in range(kp)]).synchronize()
-        te = maxall(time.perf_counter() - t0)
-        e2e = {"value": world * lups * kp / te / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "steps": kp,
+        passes = []
+        for _ in range(3):  # the host link is shared with the node's other work: median of 3 passes
+            barrier()
+            t0 = time.perf_counter()
+            pipe.run([host_in] * kp, [host_out[i % 2] for i in range(kp)]).synchronize()
+            passes.append(world * lups * kp / maxall(time.perf_counter() - t0) / 1e9)
+        e2e = {"value": sorted(passes)[1], "unit": "GLUP/s", "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": kp, "passes": passes,
                "how": "public API, page-locked host buffers, one job (H2D u0, run(T), D2H u_T) per step; "
                       "copy engines stage the next input and the previous result through dense device "
                       "buffers while the sweep runs"}

@@ -27,6 +27,10 @@ import sys
 import tempfile
 import time
 
+# More hardware work queues than CUDA's default 8, so that the end-to-end pipeline's copy
+# streams and its compute stream do not land on one queue and serialise (set before CUDA starts)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 

@@ -17,6 +17,12 @@ Per job, ordered by events:
 so the compute stream holds only the sweeps and the two short device passes, and the link
 transfers of jobs i + 1 and i - 1 proceed beside the sweep of job i. Results are identical
 to running the jobs one by one (the same kernels on the same values).
+
+The three streams must reach the GPU through different hardware work queues, or the queue
+serialises them (a sweep then waits for an unrelated copy out: measured 515-549 GLUP/s at
+1024^3 with CUDA's default of 8 queues in a process with many streams, 614-638 with 32).
+Processes that create many streams should set CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32) before
+CUDA starts; ``bench.py`` does.
 """
 from __future__ import annotations
 

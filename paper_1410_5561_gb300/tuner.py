@@ -29,6 +29,17 @@ def one_warp_xtile(dw: int, r: int, v: int) -> int:
     return max(v, (32 - 2 * ov) * v)
 
 
+def items_per_warp(t: Tuning, r: int, v: int) -> int:
+    """Work items per warp of a blocked tuning, as the library splits a full diamond: D_w^2/(2R)
+    row updates per level set, grouped in items of 2 rows (R = 1) or 1 row, each 32-vector
+    chunk of the x-tile row (trapezoid overlap included) its own item."""
+    lt = t.dw // r - 1
+    ov = -(-r * (lt - 1) // v) if lt > 1 else 0
+    nch = -(-(t.xtile // v + 2 * ov) // 32)
+    items = (t.dw * t.dw // (2 * r)) // (2 if r == 1 else 1) * nch
+    return -(-items // t.warps)
+
+
 def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tuning]:
     """Tunings that fit shared memory, best model code balance first."""
     r = RADIUS[s.kind]
@@ -54,10 +65,10 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
     kind = _KIND_NAME[s.kind]
     fdt = _DT_NAME[s.dtype]
     cdt = _DT_NAME[s.coef_dtype]
-    # measured order of merit on GB300: D_w near 8R (the largest width whose rings leave room for
-    # 16 warps), 16 warps, two frontlines, then the share of computed x columns that are useful
-    # (each x tile computes whole 32-vector chunks of its row, overlap included); the model code
-    # balance (Eq. 5) breaks ties
+    # measured order of merit on GB300: one item per warp, D_w near 8R (the largest width whose
+    # rings leave room for 16 warps), 16 warps, two frontlines, then the share of computed x
+    # columns that are useful (each x tile computes whole 32-vector chunks of its row, overlap
+    # included); the model code balance (Eq. 5) breaks ties
     def chunks(t):
         lt = t.dw // r - 1
         ov = -(-r * (lt - 1) // v) if lt > 1 else 0
@@ -67,8 +78,12 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
         return s.nx / (-(-s.nx // t.xtile) * chunks(t) * 32 * v)
 
     def score(t):
-        return (abs(t.dw - 8 * r), -t.warps, -t.nf, -round(useful(t), 3), chunks(t), -t.xtile,
-                model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw))
+        # register capacity first (the GPU analog of the paper's cache-size pruning with
+        # Eq. 3): with R = 1 each warp keeps its items' z-windows in registers, and tunings
+        # that give a warp more than one item spill under the 128-register cap of 512-thread
+        # CTAs (measured 2.4-11x slower at 512^3; they stay as a last resort)
+        return (r == 1 and items_per_warp(t, r, v) > 1, abs(t.dw - 8 * r), -t.warps, -t.nf,
+                -round(useful(t), 3), chunks(t), -t.xtile, model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw))
     out.sort(key=score)
     return out
 

@@ -1,0 +1,69 @@
+"""Autotuner candidate generation on the CPU: the library's own shared-memory figure (a
+handle needs no GPU), items per warp as the library splits a diamond, and the ranking."""
+import ctypes
+import types
+
+import pytest
+import torch
+
+from paper_1410_5561_gb300 import _lib as C
+from paper_1410_5561_gb300 import tuner
+from paper_1410_5561_gb300.stencil import Tuning
+
+OPTIN = 232448  # GB300: 227 KB of shared memory per CTA (opt-in)
+
+
+class HostGrid:
+    """The parts of a Stencil that candidate generation reads, on a host-only handle."""
+
+    def __init__(self, kind, nx, ny, nz, dtype=torch.float32):
+        self.kind, self.nx, self.ny, self.nz = kind, nx, ny, nz
+        self.dtype = self.coef_dtype = dtype
+        self.device = "cpu"
+        dt = {torch.float32: C.STENCIL_F32, torch.float64: C.STENCIL_F64}[dtype]
+        self._h = ctypes.c_void_p()
+        C.call("stencil_create", ctypes.byref(self._h), kind, nx, ny, nz, dt, dt, None)
+
+    def blocked_smem_bytes(self, t):
+        tt = t.c()
+        return int(C.lib().stencil_blocked_smem_bytes(self._h, ctypes.byref(tt)))
+
+    def close(self):
+        C.lib().stencil_destroy(self._h)
+
+
+@pytest.fixture
+def optin(monkeypatch):
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda d=None: types.SimpleNamespace(shared_memory_per_block_optin=OPTIN))
+
+
+def test_items_per_warp_matches_the_kernels_launched():
+    # (tuning, K) pairs as the launch list and the diamond-width sweep show them instantiated
+    # (the library instantiates K = 1, 2 or 4 and rounds the item count per warp up to those)
+    def inst(k):
+        return 1 if k <= 1 else (2 if k <= 2 else 4)
+
+    for t, k in [(Tuning(8, 2, 16, 104), 1), (Tuning(8, 2, 16, 112), 1), (Tuning(8, 2, 16, 128), 2),
+                 (Tuning(8, 1, 16, 256), 4), (Tuning(10, 2, 16, 64), 2), (Tuning(12, 1, 16, 104), 4),
+                 (Tuning(6, 2, 16, 104), 1), (Tuning(8, 2, 8, 104), 2), (Tuning(4, 2, 4, 120), 1)]:
+        assert inst(tuner.items_per_warp(t, 1, 4)) == k, t
+    # R = 4, one row per item: D_w = 16 gives 32 rows, x tile 32 plus 2 x 8 overlap = 12 vectors
+    assert tuner.items_per_warp(Tuning(16, 1, 16, 32), 4, 4) == 2
+
+
+def test_candidates_fit_and_put_one_item_per_warp_first(optin):
+    g = HostGrid(C.STENCIL_7PT_CONST, 1024, 1024, 1024)
+    try:
+        cands = tuner.candidates(g)
+        assert cands
+        for t in cands:
+            assert 0 < g.blocked_smem_bytes(t) <= OPTIN
+        ks = [tuner.items_per_warp(t, 1, 4) for t in cands]
+        first_multi = next((i for i, k in enumerate(ks) if k > 1), len(ks))
+        assert all(k > 1 for k in ks[first_multi:])  # every one-item tuning ranks first
+        assert first_multi >= 6                        # the benchmark times the first six
+        top = cands[0]
+        assert (top.dw, top.nf, top.warps) == (8, 2, 16)
+    finally:
+        g.close()

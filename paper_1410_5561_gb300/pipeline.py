@@ -44,11 +44,12 @@ class Pipeline:
         self.h2d = torch.cuda.Stream(dev)
         self.d2h = torch.cuda.Stream(dev)
 
-    def run(self, inputs: list[torch.Tensor], outputs: list[torch.Tensor]) -> torch.cuda.Event:
+    def run(self, inputs: list[torch.Tensor], outputs: list[torch.Tensor], trace: bool = False) -> torch.cuda.Event:
         """Advance every ``inputs[i]`` (page-locked host, (nz, ny, nx)) by T steps into
         ``outputs[i]`` (page-locked host; a buffer listed twice ends up holding the later job's
         result). Returns the event recorded after the last copy out; the outputs are valid once
-        it has completed."""
+        it has completed. ``trace``: also record timing events at every phase boundary; after
+        completion ``timeline()`` gives each job's phases in milliseconds from the start."""
         if len(inputs) != len(outputs):
             raise ValueError("one output per input")
         g = self.grid
@@ -63,26 +64,55 @@ class Pipeline:
             st.wait_event(start)
         consumed = emptied = last = None
         g.set_stream(self.compute)
+        self._trace = [] if trace else None
+        t0 = self._mark(cur)
+
         for src, dst in zip(inputs, outputs):
+            ev = {}
             with torch.cuda.stream(self.h2d):
                 if consumed is not None:
                     self.h2d.wait_event(consumed)
+                ev["h2d"] = self._mark(self.h2d)
                 self.staging_in.copy_(src, non_blocking=True)
+                ev["h2d_end"] = self._mark(self.h2d)
                 loaded = self.h2d.record_event()
             self.compute.wait_event(loaded)
+            ev["set"] = self._mark(self.compute)
             g.set_field(self.staging_in, halo=self.halo)
             consumed = self.compute.record_event()
+            ev["run"] = self._mark(self.compute)
             g.run(self.T)
+            ev["run_end"] = self._mark(self.compute)
             if emptied is not None:
                 self.compute.wait_event(emptied)
             g.get_field(self.staging_out)
             ready = self.compute.record_event()
             with torch.cuda.stream(self.d2h):
                 self.d2h.wait_event(ready)
+                ev["d2h"] = self._mark(self.d2h)
                 dst.copy_(self.staging_out, non_blocking=True)
+                ev["end"] = self._mark(self.d2h)
                 emptied = last = self.d2h.record_event()
+            if self._trace is not None:
+                self._trace.append(ev)
+        self._t0 = t0
         for st in (self.h2d, self.compute, self.d2h):
             cur.wait_stream(st)
         g.set_stream(saved)
         saved.wait_stream(cur)
         return last
+
+    def _mark(self, stream):
+        if getattr(self, "_trace", None) is None:
+            return None
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    def timeline(self) -> list[dict]:
+        """Per job of the last traced run: start and end of its copy in, load, sweep, end of sweep,
+        start and end of its copy out, in ms from the start of the run (events must have
+        completed)."""
+        if not self._trace:
+            return []
+        return [{k: self._t0.elapsed_time(e) for k, e in ev.items()} for ev in self._trace]

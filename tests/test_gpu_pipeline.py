@@ -48,9 +48,16 @@ def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T):
         assert torch.equal(a, b)
     # a second pass through the same pipeline (halo kept, grid reused) gives the same
     outs2 = [torch.empty_like(u).pin_memory() for u in jobs]
-    pipe.run(jobs[::-1], outs2).synchronize()
+    pipe.run(jobs[::-1], outs2, trace=True).synchronize()
     for a, b in zip(outs2, want[::-1]):
         assert torch.equal(a, b)
+    # the traced phases are ordered as the events that link the streams require
+    tl = pipe.timeline()
+    assert len(tl) == len(jobs)
+    for i, j in enumerate(tl):
+        assert j["h2d"] <= j["h2d_end"] <= j["set"] <= j["run"] <= j["run_end"] <= j["d2h"] <= j["end"]
+        if i:
+            assert j["run"] >= tl[i - 1]["run_end"] and j["h2d"] >= tl[i - 1]["set"]
     # the grid is back on its own stream and usable one job at a time
     s.set_field(jobs[0], halo=p.halo)
     s.run(T)

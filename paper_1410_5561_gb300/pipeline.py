@@ -23,6 +23,15 @@ serialises them (a sweep then waits for an unrelated copy out: measured 515-549 
 1024^3 with CUDA's default of 8 queues in a process with many streams, 614-638 with 32).
 Processes that create many streams should set CUDA_DEVICE_MAX_CONNECTIONS (e.g. 32) before
 CUDA starts; ``bench.py`` does.
+
+The copy engines' rate to page-locked host memory differs between machines of the same kind
+(measured 200 GB/s per direction on some GB300 machines, 40-70 GB/s on others), while the
+library's copy kernel, which keeps many SM loads in flight, held about 200 GB/s on all of
+them. Where the copy engines are slow the staged mode loses to running the jobs one by one
+with the copy kernel ("direct" mode: set_field / run / get_field from and to the host). With
+``mode="auto"`` the first call times both on its first input (three staged jobs, whose
+steady-state cost per job is the distance between consecutive sweeps, against one direct
+job) and keeps the faster; ``calibration`` records the figures.
 """
 from __future__ import annotations
 
@@ -32,10 +41,17 @@ from .stencil import Stencil
 
 
 class Pipeline:
-    def __init__(self, grid: Stencil, T: int, halo: float = 0.0):
+    MODES = ("auto", "staged", "direct")
+
+    def __init__(self, grid: Stencil, T: int, halo: float = 0.0, mode: str = "auto"):
+        if mode not in self.MODES:
+            raise ValueError(f"mode must be one of {self.MODES}")
         self.grid = grid
         self.T = int(T)
         self.halo = float(halo)
+        self.mode = mode
+        self.calibration = None
+        self._trace = None
         dev = grid.device
         shape = (grid.nz, grid.ny, grid.nx)
         self.staging_in = torch.empty(shape, dtype=grid.dtype, device=dev)
@@ -57,6 +73,47 @@ class Pipeline:
             if t.device.type != "cpu" or not t.is_pinned() or t.dtype != g.dtype or not t.is_contiguous():
                 raise ValueError("inputs and outputs must be contiguous page-locked host tensors of the "
                                  "grid's dtype")
+        if not inputs:
+            return None
+        if self.mode == "auto":
+            self._calibrate(inputs[0], outputs[0])
+        if self.mode == "direct":
+            return self._run_direct(inputs, outputs, trace)
+        return self._run_staged(inputs, outputs, trace)
+
+    def _calibrate(self, src: torch.Tensor, dst: torch.Tensor):
+        import time
+        dev = self.grid.device
+        self._run_staged([src] * 3, [dst] * 3, trace=True).synchronize()
+        tl = self.timeline()
+        staged = (tl[2]["run"] - tl[0]["run"]) / 2
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        self._run_direct([src], [dst], False).synchronize()
+        direct = 1e3 * (time.perf_counter() - t0)
+        self.mode = "staged" if staged <= direct else "direct"
+        self.calibration = {"staged_ms_per_job": staged, "direct_ms_per_job": direct, "chosen": self.mode}
+
+    def _run_direct(self, inputs, outputs, trace: bool):
+        """One job at a time on the grid's stream; the library's copy kernel moves the host data."""
+        g = self.grid
+        self._trace = [] if trace else None
+        t0 = self._mark(g.stream)
+        for src, dst in zip(inputs, outputs):
+            ev = {"h2d": self._mark(g.stream)}
+            g.set_field(src, halo=self.halo)
+            ev["h2d_end"] = ev["set"] = ev["run"] = self._mark(g.stream)
+            g.run(self.T)
+            ev["run_end"] = ev["d2h"] = self._mark(g.stream)
+            g.get_field(dst)
+            ev["end"] = self._mark(g.stream)
+            if self._trace is not None:
+                self._trace.append(ev)
+        self._t0 = t0
+        return g.stream.record_event()
+
+    def _run_staged(self, inputs, outputs, trace: bool):
+        g = self.grid
         saved = g.stream
         cur = torch.cuda.current_stream(g.device)
         start = cur.record_event()
@@ -103,7 +160,7 @@ class Pipeline:
         return last
 
     def _mark(self, stream):
-        if getattr(self, "_trace", None) is None:
+        if self._trace is None:
             return None
         e = torch.cuda.Event(enable_timing=True)
         e.record(stream)

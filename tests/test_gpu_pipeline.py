@@ -32,7 +32,8 @@ def _sequential(p, jobs, T, scheme, tn, halo):
     ("25pt_var", (29, 24, 22), "f64", None, "plain", None),
 ])
 @pytest.mark.parametrize("T", [1, 8])
-def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T):
+@pytest.mark.parametrize("mode", ["staged", "direct", "auto"])
+def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T, mode):
     p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=21, halo=0.25)
     tdt = {"f32": torch.float32, "f64": torch.float64}[fdt]
     g = torch.Generator().manual_seed(5)
@@ -42,8 +43,10 @@ def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T):
     s = p.make()
     s.set_tuning(scheme, tn)
     outs = [torch.empty_like(u).pin_memory() for u in jobs]
-    pipe = Pipeline(s, T, halo=p.halo)
+    pipe = Pipeline(s, T, halo=p.halo, mode=mode)
     pipe.run(jobs, outs).synchronize()
+    if mode == "auto":  # calibrated once on the first input, then one of the two modes
+        assert pipe.mode in ("staged", "direct") and pipe.calibration["chosen"] == pipe.mode
     for a, b in zip(outs, want):
         assert torch.equal(a, b)
     # a second pass through the same pipeline (halo kept, grid reused) gives the same

@@ -15,7 +15,7 @@ import math
 import torch
 
 from . import model
-from .stencil import NCOEF, RADIUS, Stencil, Tuning
+from .stencil import RADIUS, Stencil, Tuning
 
 _CACHE: dict = {}
 _KIND_NAME = {0: "7pt_const", 1: "7pt_var", 2: "25pt_var"}

@@ -53,9 +53,7 @@ class Pipeline:
         self.calibration = None
         self._trace = None
         dev = grid.device
-        shape = (grid.nz, grid.ny, grid.nx)
-        self.staging_in = torch.empty(shape, dtype=grid.dtype, device=dev)
-        self.staging_out = torch.empty(shape, dtype=grid.dtype, device=dev)
+        self.staging_in = self.staging_out = None  # dense device arrays of the staged mode
         self.compute = torch.cuda.Stream(dev)
         self.h2d = torch.cuda.Stream(dev)
         self.d2h = torch.cuda.Stream(dev)
@@ -93,6 +91,8 @@ class Pipeline:
         direct = 1e3 * (time.perf_counter() - t0)
         self.mode = "staged" if staged <= direct else "direct"
         self.calibration = {"staged_ms_per_job": staged, "direct_ms_per_job": direct, "chosen": self.mode}
+        if self.mode == "direct":  # the staging arrays are not needed any more
+            self.staging_in = self.staging_out = None
 
     def _run_direct(self, inputs, outputs, trace: bool):
         """One job at a time on the grid's stream; the library's copy kernel moves the host data."""
@@ -114,6 +114,10 @@ class Pipeline:
 
     def _run_staged(self, inputs, outputs, trace: bool):
         g = self.grid
+        if self.staging_in is None:
+            shape = (g.nz, g.ny, g.nx)
+            self.staging_in = torch.empty(shape, dtype=g.dtype, device=g.device)
+            self.staging_out = torch.empty(shape, dtype=g.dtype, device=g.device)
         saved = g.stream
         cur = torch.cuda.current_stream(g.device)
         start = cur.record_event()

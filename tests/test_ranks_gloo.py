@@ -54,3 +54,19 @@ def test_single_process_needs_no_process_group(monkeypatch):
     assert r.world == 1 and r.root and r.dist is None
     r.barrier()
     assert r.maxall(3.5) == 3.5 and r.aggregate(10.0, 2.0) == 5.0
+
+
+def test_pipeline_summary_of_a_timeline():
+    """The e2e phase summary: mean sweep, gap between sweeps, copies, exposed ends."""
+    jobs = []
+    for i in range(3):
+        r = 10.0 + 160.0 * i
+        jobs.append({"h2d": r - 30.0, "h2d_end": r - 10.0, "set": r - 2.0, "run": r, "run_end": r + 150.0,
+                     "d2h": r + 152.0, "end": r + 180.0})
+    out = bench.pipeline_summary(jobs)
+    assert out["sweep"] == 150.0
+    assert out["gap_between_sweeps"] == 10.0
+    assert out["copy_in"] == 20.0 and out["copy_out"] == 28.0
+    assert out["first_sweep_start"] == 10.0 and out["after_last_sweep"] == 30.0
+    assert out["total"] == jobs[-1]["end"]
+    assert bench.pipeline_summary([]) is None

@@ -63,6 +63,9 @@ def test_pipeline_summary_of_a_timeline():
         r = 10.0 + 160.0 * i
         jobs.append({"h2d": r - 30.0, "h2d_end": r - 10.0, "set": r - 2.0, "run": r, "run_end": r + 150.0,
                      "d2h": r + 152.0, "end": r + 180.0})
+    spec = importlib.util.spec_from_file_location("bench_summary", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
     out = bench.pipeline_summary(jobs)
     assert out["sweep"] == 150.0
     assert out["gap_between_sweeps"] == 10.0

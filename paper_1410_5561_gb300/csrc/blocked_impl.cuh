@@ -80,6 +80,7 @@ struct GridArgs {
     const TC* C[13];
     TF c0, c1, halo;
     int p0, T, D, Xt, EH, Xs, CX;
+    int Xe;  // width of the first and last x tiles (Xt, or Xt plus the one-sided overlap)
 };
 
 // Row launch: every tile (row, bmin + blockIdx.y) of one diamond row, x tile blockIdx.x.
@@ -278,7 +279,11 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     // ring depth (planes per level): with register windows the ring is read from the
     // current plane up, otherwise from R planes below it
     constexpr int Q = PERSIST ? 3 * NF + R : 3 * NF + 2 * R;
-    const int x0 = xti * Xt;
+    // x tiles: interior tiles are Xt wide; with R = 1 the first and last tiles, which need no
+    // trapezoid overlap on the grid's side, are Xe = Xt + overlap wide (the host sets Xe = Xt
+    // otherwise), so their rows fit the same lanes
+    const int x0 = xti == 0 ? 0 : P.Xe + (xti - 1) * Xt;
+    const int Wt = (xti == 0 || xti == P.CX - 1) ? P.Xe : Xt;
     const int Ny = L.ny, Nz = L.nz, Nx = L.nx;
     __syncthreads();  // the previous tile of this CTA has finished with M and the ring
     const int rnx = ((Nx + V - 1) / V) * V;
@@ -306,16 +311,19 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             M.nhi[l] = nhi;
             M.roff[l] = off;
             off += Q * (nhi - nlo) * Xs;
-            // x extent: level l computes [x0 - e, x0 + Xt + e), e = R (Lt - 1 - l),
-            // clipped to [-HV, rnx + HV); its input spans R more on each side.
+            // x extent: level l computes [x0 - e, x0 + Wt + e), e = R (Lt - 1 - l), clipped
+            // to the vectors that hold interior columns when the ring is prefilled with the
+            // Dirichlet value (R = 1), else to [-HV, rnx + HV); its input spans R more on each
+            // side.
             const int e = R * (Lt - 1 - l);
-            int xl = x0 - e, xh = x0 + Xt + e;
-            if (xl < -HV) xl = -HV;
-            if (xh > rnx + HV) xh = rnx + HV;
+            const int clo = PERSIST ? 0 : -HV, chi = PERSIST ? rnx : rnx + HV;
+            int xl = x0 - e, xh = x0 + Wt + e;
+            if (xl < clo) xl = clo;
+            if (xh > chi) xh = chi;
             M.xlo[l] = xl;
             M.xhi[l] = xh;
             M.vlo[l] = fdiv(xl - x0 + EH, V);
-            int il_ = x0 - e - R, ih_ = x0 + Xt + e + R;
+            int il_ = x0 - e - R, ih_ = x0 + Wt + e + R;
             if (il_ < -HV) il_ = -HV;
             if (ih_ > rnx + HV) ih_ = rnx + HV;
             M.ldlo[l] = fdiv(il_ - x0 + EH, V);
@@ -412,7 +420,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             I.hasd[i] = nxt && y >= M.nlo[l + 1] && y < M.nhi[l + 1];
             I.ad[i] = I.hasd[i] ? smem_u32(ring + M.roff[l + 1] + (y - M.nlo[l + 1]) * Xs + v * V) : 0u;
             I.store[i] = i < I.nr && I.active && I.indom && !(y >= M.wlo[l] && y < M.whi[l]) && I.xg >= x0 &&
-                         I.xg < x0 + Xt;
+                         I.xg < x0 + Wt;
             I.g0[i] = I.indom ? (uint32_t)L.at(I.xg, y, 0) : 0u;
         }
         I.gdst = P.f[(p0 + M.t0 + l + 1) & 1];
@@ -997,6 +1005,7 @@ static int item_bound(int D, int R) { return D * D / (2 * R); }
 
 struct BlkShape {
     int V, HV, Xt, EH, Xs, Q, K, nch;
+    int Xe, CX;  // width of the first and last x tiles, x tiles per row
     size_t smem;
     bool ok;
 };
@@ -1023,8 +1032,21 @@ static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps
     if (ltmax > MAXLV) return s;
     if (warps < 1 || warps * 32 > BLK_MAXT) return s;
     if (xtile < s.V || xtile % s.V != 0 || xtile > 4096) return s;
-    if ((nx + xtile - 1) / xtile > MAXCLUSTER) return s;
     int ov = ltmax > 1 ? (R * (ltmax - 1) + s.V - 1) / s.V : 0;
+    // x tiles per row: one when the row fits; else, with R = 1, two edge tiles of xtile + ov V
+    // columns (no overlap on the grid's side; the same lanes as an interior tile) around
+    // ceil((nx - 2 Xe) / xtile) interior tiles; with R = 4, ceil(nx / xtile) equal tiles
+    if (nx <= xtile) {
+        s.CX = 1;
+        s.Xe = xtile;
+    } else if (R == 1) {
+        s.Xe = xtile + ov * s.V;
+        s.CX = nx <= 2 * s.Xe ? 2 : 2 + (nx - 2 * s.Xe + xtile - 1) / xtile;
+    } else {
+        s.Xe = xtile;
+        s.CX = (nx + xtile - 1) / xtile;
+    }
+    if (s.CX > MAXCLUSTER) return s;
     s.nch = (xtile / s.V + 2 * ov + 31) / 32;
     // rows per item, as in the kernel; unclipped widths are multiples of 2R, and clipping
     // only removes rows, so ceil(w / rb) summed over the levels never exceeds D^2/(2R rb)
@@ -1037,7 +1059,7 @@ static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps
     s.K = K <= 1 ? 1 : (K <= 2 ? 2 : 4);
     s.Xt = xtile;
     s.EH = ((R * ltmax + s.V - 1) / s.V) * s.V + s.HV;
-    s.Xs = s.Xt + 2 * s.EH;
+    s.Xs = s.Xe + 2 * s.EH;  // the widest tile's ring row
     s.Q = R == 1 ? 3 * nf + R : 3 * nf + 2 * R;  // matches the kernel's ring depth
     s.smem = (size_t)s.Q * ring_rows_bound(dw, R) * s.Xs * eb;
     s.ok = true;
@@ -1073,6 +1095,7 @@ static GridArgs<TF, TC> grid_args(const SweepArgs& a, void* const field[2], int 
     G.T = T;
     G.D = tn.dw;
     G.Xt = sh.Xt;
+    G.Xe = sh.Xe;
     G.EH = sh.EH;
     G.Xs = sh.Xs;
     G.CX = 1;
@@ -1086,7 +1109,7 @@ static cudaError_t launch_blocked_k(const SweepArgs& a, void* const field[2], in
     auto kfn = blocked_kernel<KIND, TF, TC, K, NF>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
     if (e != cudaSuccess) return e;
-    const int nxt = (a.L.nx + sh.Xt - 1) / sh.Xt;
+    const int nxt = sh.CX;
     if (nxt > 8) {
         e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
@@ -1448,7 +1471,7 @@ static cudaError_t persist_k(const SweepArgs& a, void* const field[2], int p0, i
     auto kfn = blocked_persist_kernel<KIND, TF, TC, K, NF>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
     if (e) return e;
-    const int nxt = (a.L.nx + sh.Xt - 1) / sh.Xt;
+    const int nxt = sh.CX;
     if (nxt > 8 && (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1))) return e;
     cudaLaunchConfig_t cfg{};
     cfg.blockDim = dim3((unsigned)(tn.warps * 32), 1, 1);

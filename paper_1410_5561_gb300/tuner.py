@@ -40,6 +40,20 @@ def items_per_warp(t: Tuning, r: int, v: int) -> int:
     return -(-items // t.warps)
 
 
+def x_tiles(nx: int, t: Tuning, r: int, v: int) -> int:
+    """x tiles per row as the library cuts them: one if the row fits, else (R = 1) two edge
+    tiles of xtile plus the one-sided trapezoid overlap around interior tiles of xtile, or
+    (R = 4) equal tiles."""
+    if nx <= t.xtile:
+        return 1
+    if r != 1:
+        return -(-nx // t.xtile)
+    lt = t.dw // r - 1
+    ov = -(-r * (lt - 1) // v) if lt > 1 else 0
+    xe = t.xtile + ov * v
+    return 2 if nx <= 2 * xe else 2 + -(-(nx - 2 * xe) // t.xtile)
+
+
 def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tuning]:
     """Tunings that fit shared memory, best model code balance first."""
     r = RADIUS[s.kind]
@@ -75,7 +89,7 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
         return -(-(t.xtile // v + 2 * ov) // 32)
 
     def useful(t):
-        return s.nx / (-(-s.nx // t.xtile) * chunks(t) * 32 * v)
+        return s.nx / (x_tiles(s.nx, t, r, v) * chunks(t) * 32 * v)
 
     def score(t):
         # register capacity first (the GPU analog of the paper's cache-size pruning with

@@ -67,6 +67,12 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
         xts = {xt, max(v, (xt // 2) // v * v)}
         ntile = -(-s.nx // xt)  # the same number of x tiles, evenly wide
         xts.add(max(v, -(-(-(-s.nx // ntile)) // v) * v))
+        if r == 1 and s.nx > xt:  # the narrowest tiles that keep the uneven split's tile count
+            nt = x_tiles(s.nx, Tuning(dw, 1, 16, xt), r, v)
+            lt = dw // r - 1
+            ov = -(-r * (lt - 1) // v) if lt > 1 else 0
+            if nt > 2:
+                xts.add(max(v, -(-(-(-(s.nx - 2 * ov * v) // nt)) // v) * v))
         for nclu in (2, 4, 8):  # x tiles splitting the row into portable cluster sizes
             xts.add(max(v, ((s.nx + nclu - 1) // nclu + v - 1) // v * v))
         for xtile in sorted(xts, reverse=True):

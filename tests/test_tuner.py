@@ -67,3 +67,16 @@ def test_candidates_fit_and_put_one_item_per_warp_first(optin):
         assert (top.dw, top.nf, top.warps) == (8, 2, 16)
     finally:
         g.close()
+
+
+def test_tight_uneven_tiles_are_candidates(optin):
+    """With R = 1 the edge tiles carry one-sided overlap; the width that covers the row with the
+    fewest tiles and the least waste is offered (512: 100 columns; 1024: 112)."""
+    for n, want in [(512, 100), (1024, 112)]:
+        g = HostGrid(C.STENCIL_7PT_CONST, n, 64, 64)
+        try:
+            xs = {t.xtile for t in tuner.candidates(g) if (t.dw, t.nf, t.warps) == (8, 2, 16)}
+            assert want in xs, (n, sorted(xs))
+            assert tuner.x_tiles(n, Tuning(8, 2, 16, want), 1, 4) == (5 if n == 512 else 9)
+        finally:
+            g.close()

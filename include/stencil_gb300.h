@@ -74,7 +74,7 @@ enum stencil_status {
 };
 
 /* Blocked-schedule tunables (Section II-A, III-A): dw = diamond width D_w
- * along y (a multiple of 2R with D_w/R - 1 <= 32 time levels), nf = frontlines
+ * along y (a multiple of 2R with D_w/R - 1 <= 64 time levels), nf = frontlines
  * N_F (z planes per time level per wavefront step: 1 or 2), warps = warps per
  * CTA (1..16; the CTA is the thread group that shares one extruded diamond),
  * xtile = x columns one CTA owns (a multiple of 16 bytes' worth of field
@@ -82,7 +82,8 @@ enum stencil_status {
  * wider than xtile is split into tiles that run as one thread-block cluster
  * (at most 16); for the 7-point stencils the first and last tiles of a row
  * are wider by the trapezoid overlap they need on one side only. Tunings whose
- * rings exceed the shared memory of one CTA, or whose items exceed 4 per warp,
+ * rings exceed the shared memory of one CTA, whose items exceed 4 per warp, or
+ * whose diamonds hold more than 256 computed or loaded rows per x-tile chunk,
  * are rejected (STENCIL_ENOSMEM / STENCIL_EINVAL). */
 typedef struct {
     int dw;

@@ -120,9 +120,45 @@ def peaks():
 
 # ----------------------------------------------------------------- CPU oracle arm
 
-def cpu_oracle_sample(budget_s: float = 15.0, n: int = CPU_BASELINE_N, seed: int = 0):
+def host_description():
+    """The host cores the CPU baseline runs on: logical CPUs, the ones this process may
+    use (affinity), the CPU model and the clock the kernel reports."""
+    info = {"nproc": os.cpu_count()}
+    try:
+        info["affinity_cpus"] = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        info["affinity_cpus"] = None
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    info["cpu_model"] = model
+    for key, fname in (("max_mhz", "cpuinfo_max_freq"), ("cur_mhz", "scaling_cur_freq")):
+        p = f"/sys/devices/system/cpu/cpu0/cpufreq/{fname}"
+        try:
+            with open(p) as f:
+                info[key] = int(f.read().strip()) / 1000.0
+        except (OSError, ValueError):
+            info[key] = None
+    return info
+
+
+def cpu_oracle_sample(budget_s: float = 15.0, n: int = CPU_BASELINE_N, seed: int = 0,
+                      single_core_s: float = 5.0):
     """Time the FP64 oracle (7-point constant, Listing 1) on an n^3 sample on the host
-    cores; T is chosen so the sample takes about ``budget_s`` seconds."""
+    cores; T is chosen so the sample takes about ``budget_s`` seconds. A second, single-core
+    run at reduced T (about ``single_core_s`` seconds) is reported beside it."""
     import oracle
     from paper_1410_5561_gb300 import inputs
     u0 = inputs.field_u0(seed, n, n, n)
@@ -140,8 +176,19 @@ def cpu_oracle_sample(budget_s: float = 15.0, n: int = CPU_BASELINE_N, seed: int
     oracle.sweep("7pt_const", u0, T)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # one core, reduced T (stated)
+    t0 = time.perf_counter()
+    oracle.sweep("7pt_const", u0, 1, nthreads=1)
+    t1s = max(time.perf_counter() - t0, 1e-3)
+    T1 = max(1, min(50, int(single_core_s / t1s)))
+    t0 = time.perf_counter()
+    oracle.sweep("7pt_const", u0, T1, nthreads=1)
+    dt1 = time.perf_counter() - t0
     return {"value": n ** 3 * T / dt / 1e9, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
-            "sample": f"7pt-const FP64 oracle, {n}^3 interior, T={T} steps ({dt:.1f} s), OpenMP over k"}
+            "sample": f"7pt-const FP64 oracle, {n}^3 interior, T={T} steps ({dt:.1f} s), OpenMP over k",
+            "host": host_description(),
+            "single_core": {"value": n ** 3 * T1 / dt1 / 1e9, "unit": "GLUP/s", "cores": 1,
+                            "sample": f"same grid, T={T1} steps ({dt1:.1f} s, reduced T), one thread"}}
 
 
 def run_reference(args):
@@ -566,36 +613,110 @@ PER_STENCIL = [
     ("7pt_var", 384, "f32", "bf16", 50),
     ("7pt_var", 384, "f64", None, 50),
     ("25pt_var", 256, "f32", None, 40),
+    ("25pt_var", 256, "f32", "bf16", 40),
+    ("25pt_var", 256, "f64", None, 40),
 ]
 
 
+def sampled_oracle_error(s, kind, n, fdt, cdt, T, seed):
+    """Error of the grid's current field (u_T from the seeded u0) against the FP64 oracle
+    at a few sampled points: each point's u_T is evaluated by ``oracle.points`` on a crop of
+    the host-drawn inputs reaching R*T + R cells past it (clipped at the grid's Dirichlet
+    faces), in the precisions the device stores. Returns the step-normalised L2 over the
+    points, ||g - ref|| / (||ref|| T), and the largest relative error; for BF16 coefficients
+    also the "storage error": the same against the oracle on the unrounded FP64
+    coefficients (stated, not gated)."""
+    import numpy as np
+    import oracle
+    from paper_1410_5561_gb300 import inputs
+    R = 4 if kind == "25pt_var" else 1
+    m = R * T + R
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (n - 1, 0, n // 2)]
+    if 2 * m + 1 < n:
+        pts.append((n // 2, n // 3, n // 5))
+    sc = (0.4, 0.1)
+    if fdt == "f32":
+        sc = (float(np.float32(0.4)), float(np.float32(0.1)))
+    got = s.current
+    g, ref, ref_unrounded = [], [], []
+    for (i, j, k) in pts:
+        lo = tuple(max(0, c - m) for c in (k, j, i))
+        hi = tuple(min(n, c + m + 1) for c in (k, j, i))
+        u0 = inputs.field_u0_box(seed, n, n, n, lo, hi)
+        if fdt == "f32":
+            u0 = inputs.round_f32(u0)
+        loc = [(i - lo[2], j - lo[1], k - lo[0])]
+        coefs = c64 = None
+        if kind != "7pt_const":
+            c64 = inputs.coefs_box(kind, seed, n, n, n, lo, hi)
+            st = cdt or fdt
+            coefs = inputs.bf16_to_f64(inputs.bf16_bits(c64)) if st == "bf16" else (
+                inputs.round_f32(c64) if st == "f32" else c64)
+        ref.append(oracle.points(kind, u0, T, loc, coefs=coefs, scalars=sc)[0])
+        if cdt == "bf16":
+            ref_unrounded.append(oracle.points(kind, u0, T, loc, coefs=c64, scalars=sc)[0])
+        g.append(float(got[k, j, i]))
+    g, ref = np.array(g), np.array(ref)
+
+    def errs(r):
+        den = np.linalg.norm(r) * max(T, 1)
+        return {"step_normalised_l2": float(np.linalg.norm(g - r) / den) if den > 0 else None,
+                "max_rel": float(np.max(np.abs(g - r)) / max(float(np.max(np.abs(r))), 1e-300))}
+
+    out = {"points": len(pts), **errs(ref),
+           "gate": 1e-5 if fdt == "f32" else 1e-12}
+    out["within_gate"] = out["step_normalised_l2"] is not None and out["step_normalised_l2"] <= out["gate"]
+    if cdt == "bf16":
+        out["storage_error_vs_unrounded_coefficients"] = errs(np.array(ref_unrounded))
+    return out
+
+
 def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
+    """Plain vs tuned blocked sweep for every stencil and precision: GLUP/s, the model bytes
+    per LUP, the roofline (the slower of the HBM bound at the model bytes and the FP-pipe
+    bound) and the achieved fraction of it, and each result's error against the FP64 oracle
+    on sampled points."""
     import torch
     from paper_1410_5561_gb300 import model, tuner
     rows = []
     for kind, n, fdt, cdt, T in PER_STENCIL:
         s, u0 = make_grid(kind, n, fdt, cdt, seed, device)
         lups = float(n) ** 3 * T
+        bp = model.bytes_per_lup(kind, fdt, cdt, "plain")
+        peak_fp = fp64_peak if fdt == "f64" else fp32_peak
+        alu_glups = peak_fp / (model.FP_INSTR[kind] * 2) / 1e9
         s.set_tuning("plain")
         tp = timed(s, T, 2, 1) / 2
+        s.set_field(u0, halo=0.0)
+        s.run(T)
+        err_plain = sampled_oracle_error(s, kind, n, fdt, cdt, T, seed)
         try:
             tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
             tb = timed(s, T, 2, 1) / 2
             tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
             bb = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)
+            s.set_field(u0, halo=0.0)
+            s.run(T)
+            err_blk = sampled_oracle_error(s, kind, n, fdt, cdt, T, seed)
         except RuntimeError:
-            tb, tun, bb = None, None, None
-        bp = model.bytes_per_lup(kind, fdt, cdt, "plain")
-        peak_fp = fp64_peak if fdt == "f64" else fp32_peak
-        alu_t = model.FP_INSTR[kind] * 2 / peak_fp
+            tb, tun, bb, err_blk = None, None, None, None
+        roof_p = min(hbm_peak / bp, alu_glups)
+        roof_b = min(hbm_peak / bb, alu_glups) if bb else None
+        gp = lups / tp / 1e9
+        gb = lups / tb / 1e9 if tb else None
         rows.append({
             "stencil": kind, "grid": n, "field": fdt, "coef": cdt or fdt, "T": T,
-            "plain_glups": lups / tp / 1e9,
-            "blocked_glups": lups / tb / 1e9 if tb else None,
+            "plain_glups": gp,
+            "blocked_glups": gb,
+            "blocked_over_plain": gb / gp if gb else None,
             "blocked_tuning": tun,
             "model_bytes_per_lup": {"plain": bp, "blocked": bb},
             "roofline_glups": {"hbm_plain": hbm_peak / bp, "hbm_blocked": hbm_peak / bb if bb else None,
-                               "alu": 1e-9 / alu_t},
+                               "alu": alu_glups},
+            "roofline_frac": {"plain": gp / roof_p, "blocked": gb / roof_b if gb else None,
+                              "plain_bound": "hbm" if hbm_peak / bp <= alu_glups else "alu",
+                              "blocked_bound": ("hbm" if hbm_peak / bb <= alu_glups else "alu") if bb else None},
+            "err_vs_oracle": {"plain": err_plain, "blocked": err_blk},
         })
         del s, u0
         torch.cuda.empty_cache()

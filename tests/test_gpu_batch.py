@@ -1,10 +1,12 @@
-"""Persistent batched launch of many grids: bitwise equal to per-grid sweeps,
-CUDA-graph capture and replay, bounded dependency waits."""
+"""Persistent batched launch of many grids: every grid against the FP64 oracle
+(element-wise bound and the step-normalised L2 gate), bitwise equal to per-grid
+plain sweeps, CUDA-graph capture and replay, bounded dependency waits."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1410_5561_gb300 import inputs
-from tests._util import Problem
+from tests._util import Problem, step_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -24,12 +26,24 @@ def _plain_result(p, T):
     return s.get_field().cpu().numpy()
 
 
+def _check_oracle(p, T, got):
+    """u_T of one grid of a batch against the FP64 oracle on the same (rounded) inputs."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = p.oracle(T)
+    assert oracle.step_normalised_l2(got, ref, T) <= step_tol(p.fdt)
+    err = float(np.max(np.abs(got - ref))) if got.size else 0.0
+    assert err <= p.elementwise_tol(T), (err, p.elementwise_tol(T))
+
+
 @pytest.mark.parametrize("kind,fdt,cdt,tn", [
     ("7pt_var", "f32", None, (8, 1, 16)),
     ("7pt_var", "f32", "bf16", (6, 2, 8)),
     ("7pt_const", "f32", None, (8, 2, 16)),
     ("7pt_const", "f64", None, (4, 1, 8)),
     ("25pt_var", "f32", None, (8, 1, 8)),
+    ("25pt_var", "f32", "bf16", (8, 2, 8)),
+    ("25pt_var", "f64", None, (8, 2, 8)),
+    ("7pt_var", "f64", None, (4, 2, 8)),
 ])
 def test_batch_bitwise_equals_plain(kind, fdt, cdt, tn):
     from paper_1410_5561_gb300.batch import Batch
@@ -40,7 +54,9 @@ def test_batch_bitwise_equals_plain(kind, fdt, cdt, tn):
     b.launch()
     assert b.status() == 0
     for (p, T), g in zip(probs, grids):
-        assert np.array_equal(g.get_field().cpu().numpy(), _plain_result(p, T))
+        got = g.get_field().cpu().numpy()
+        _check_oracle(p, T, got)
+        assert np.array_equal(got, _plain_result(p, T))
 
 
 def test_batch_graph_replay():
@@ -59,7 +75,9 @@ def test_batch_graph_replay():
     b.sync_parity()
     assert b.status() == 0
     for (p, T), g in zip(probs, grids):
-        assert np.array_equal(g.get_field().cpu().numpy(), _plain_result(p, 3 * T))
+        got = g.get_field().cpu().numpy()
+        _check_oracle(p, 3 * T, got)
+        assert np.array_equal(got, _plain_result(p, 3 * T))
 
 
 def test_batch_timeout_is_reported_not_hung():
@@ -79,7 +97,8 @@ def test_batch_timeout_is_reported_not_hung():
 
 def test_batch_full_workload_sampled():
     """The 64-grid batch (sides 32..192, T 10..200, 7-point variable FP32): a graph replay,
-    then a sample of grids checked bitwise against their own plain sweeps."""
+    then a sample of grids checked against the FP64 oracle and bitwise against their own
+    plain sweeps."""
     import torch
     from paper_1410_5561_gb300.batch import Batch
     from paper_1410_5561_gb300.stencil import Tuning
@@ -94,7 +113,9 @@ def test_batch_full_workload_sampled():
     assert b.status() == 0
     for q in (0, 7, 21, 42, 63):
         p, T = probs[q]
-        assert np.array_equal(grids[q].get_field().cpu().numpy(), _plain_result(p, T)), q
+        got = grids[q].get_field().cpu().numpy()
+        _check_oracle(p, T, got)
+        assert np.array_equal(got, _plain_result(p, T)), q
 
 
 def test_batch_autotuner_choice_is_feasible_and_exact():
@@ -115,4 +136,6 @@ def test_batch_autotuner_choice_is_feasible_and_exact():
     b.launch()
     assert b.status() == 0
     for (p, T), g in zip(probs, fresh):
-        assert np.array_equal(g.get_field().cpu().numpy(), _plain_result(p, T))
+        got = g.get_field().cpu().numpy()
+        _check_oracle(p, T, got)
+        assert np.array_equal(got, _plain_result(p, T))

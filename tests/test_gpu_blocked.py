@@ -45,10 +45,11 @@ def test_blocked_bitwise_equals_plain_r1(kind, shape, fdt, cdt, tn, T):
 
 
 @pytest.mark.parametrize("tn", R4_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xtile}")
-@pytest.mark.parametrize("shape,fdt", [((29, 35, 21), "f32"), ((18, 25, 14), "f64")])
+@pytest.mark.parametrize("shape,fdt,cdt", [((29, 35, 21), "f32", None), ((18, 25, 14), "f64", None),
+                                           ((27, 33, 19), "f32", "bf16")])
 @pytest.mark.parametrize("T", [1, 5, 9])
-def test_blocked_bitwise_equals_plain_r4(shape, fdt, tn, T):
-    p = Problem("25pt_var", *shape, fdt=fdt, seed=12, halo=-0.25)
+def test_blocked_bitwise_equals_plain_r4(shape, fdt, cdt, tn, T):
+    p = Problem("25pt_var", *shape, fdt=fdt, cdt=cdt, seed=12, halo=-0.25)
     a = _run(p, T, "plain")
     b = _run(p, T, "blocked", tn)
     assert np.array_equal(a, b)
@@ -71,14 +72,18 @@ def test_blocked_wide_x_tiles_bitwise(kind, shape, fdt, cdt, tn, T):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("kind,shape,fdt,T,tn", [
-    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(8, 1, 8, 48)),
-    ("7pt_const", (64, 64, 64), "f64", 8, Tuning(10, 1, 16, 16)),
-    ("7pt_var", (50, 47, 31), "f32", 10, Tuning(8, 1, 8, 16)),
-    ("25pt_var", (40, 33, 30), "f32", 6, Tuning(16, 1, 8, 20)),
+@pytest.mark.parametrize("kind,shape,fdt,cdt,T,tn", [
+    ("7pt_const", (64, 64, 64), "f64", None, 8, Tuning(8, 1, 8, 48)),
+    ("7pt_const", (64, 64, 64), "f64", None, 8, Tuning(10, 1, 16, 16)),
+    ("7pt_var", (50, 47, 31), "f32", None, 10, Tuning(8, 1, 8, 16)),
+    ("7pt_var", (50, 47, 31), "f32", "bf16", 10, Tuning(8, 2, 16, 24)),
+    ("7pt_var", (36, 41, 22), "f64", None, 9, Tuning(6, 1, 8, 12)),
+    ("25pt_var", (40, 33, 30), "f32", None, 6, Tuning(16, 1, 8, 20)),
+    ("25pt_var", (40, 33, 30), "f32", "bf16", 6, Tuning(16, 1, 8, 20)),
+    ("25pt_var", (26, 31, 23), "f64", None, 5, Tuning(8, 2, 8, 12)),
 ])
-def test_blocked_matches_oracle(kind, shape, fdt, T, tn):
-    p = Problem(kind, *shape, fdt=fdt, seed=13)
+def test_blocked_matches_oracle(kind, shape, fdt, cdt, T, tn):
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=13)
     got = _run(p, T, "blocked", tn).astype(np.float64)
     ref = p.oracle(T)
     assert oracle.step_normalised_l2(got, ref, T) <= step_tol(fdt)

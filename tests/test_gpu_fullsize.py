@@ -37,6 +37,7 @@ FULL = [
     ("7pt_var", 384, "f32", "bf16", 50, 4),
     ("7pt_var", 384, "f64", None, 50, 4),
     ("25pt_var", 256, "f32", None, 40, 4),
+    ("25pt_var", 256, "f32", "bf16", 40, 4),
 ]
 SEED = 0
 

@@ -118,8 +118,10 @@ int stencil_layout_of(stencil_t h, int which, stencil_layout* out);
 /* Bytes of device workspace the handle can use (caller-allocated, passed to
  * bind). With a workspace bound, the blocked schedule runs as one persistent
  * launch whose thread-block clusters walk the dependency-ordered list of
- * diamond tiles (the plan is kept in the workspace); without one (NULL) it
- * runs one launch per diamond row. */
+ * diamond tiles (Section II-A's queue of ready diamonds; the tiles are derived
+ * on the device, the workspace holds their completion counters and the
+ * status word read by stencil_status); without one (NULL) it runs one launch
+ * per diamond row and has nothing to wait on. */
 size_t stencil_workspace_bytes(stencil_t h);
 
 /* Bind caller-owned device arrays: field_a, field_b (field layout; ping-pong
@@ -149,9 +151,30 @@ int stencil_set_field(stencil_t h, const void* src, double halo_value, int where
 int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning);
 
 /* Advance the current field by T >= 0 Jacobi steps (Listings 1-3 applied T
- * times). Asynchronous on the handle's stream. Afterwards field_a holds u_T if
- * (initial parity + T) is even, field_b otherwise (see stencil_parity). */
+ * times). Asynchronous on the handle's stream: it only enqueues kernels and
+ * memsets (no host copy, no wait), so it can be captured in a CUDA graph.
+ * Afterwards field_a holds u_T if (initial parity + T) is even, field_b
+ * otherwise (see stencil_parity). A persistent blocked launch whose dependency
+ * wait runs out of its limit cannot hang: it sets the status word (see
+ * stencil_status) and the field is then undefined. */
 int stencil_run(stencil_t h, int T);
+
+/* Device error/timeout word of the handle (synchronous: waits for the
+ * handle's stream). Returns STENCIL_OK, STENCIL_ETIMEOUT if a persistent
+ * blocked launch since the last stencil_set_field (or stencil_bind) gave up a
+ * dependency wait (the field is then undefined until the next set_field),
+ * STENCIL_ECUDA on an asynchronous CUDA error, or STENCIL_EINVAL. */
+int stencil_status(stencil_t h);
+
+/* Bound on the spin iterations of one dependency wait of the persistent
+ * blocked schedule (about 0.15 us each; default 2^24, a few seconds). */
+int stencil_set_wait_limit(stencil_t h, unsigned spins);
+
+/* Test hook: in later persistent blocked launches, tile `tile` of the plan
+ * also waits on a flag that no tile sets, so that its wait runs out and
+ * stencil_status reports STENCIL_ETIMEOUT; -1 removes the stall. A tile index
+ * beyond the plan's tiles has no effect. */
+int stencil_inject_stall(stencil_t h, int tile);
 
 /* 0 if field_a holds the current time level, 1 if field_b does. */
 int stencil_parity(stencil_t h);
@@ -222,8 +245,9 @@ size_t stencil_batch_workspace_bytes(stencil_batch_t b);
 int stencil_batch_item_count(stencil_batch_t b);
 
 /* Upload the plan into workspace (device, caller-owned, 16-byte aligned,
- * stencil_batch_workspace_bytes long); synchronous on cuda_stream. The grids'
- * current parities are recorded here. */
+ * stencil_batch_workspace_bytes long); synchronous on cuda_stream, so it must
+ * not be called on a capturing stream (STENCIL_EINVAL). The grids' current
+ * parities are recorded here. */
 int stencil_batch_bind(stencil_batch_t b, void* workspace, void* cuda_stream);
 
 /* Enqueue one launch (a counter reset and the persistent kernel) on cuda_stream;
@@ -267,16 +291,21 @@ int stencil_batch_destroy(stencil_batch_t b);
  * array in device memory owned by the library, which every GPU that loads the
  * library holds until the process exits. A batch whose scratch would exceed
  * 4 MiB is rejected with STENCIL_EINVAL before anything is launched. The
- * grids' arrays are the caller's, as usual. The call uploads the plan (waiting
- * for cuda_stream), enqueues the launch on cuda_stream and updates the grids'
- * parities; if status_out is not NULL it also waits for the launch and stores
- * STENCIL_OK or STENCIL_ETIMEOUT there.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture. All calls share the one array and it keeps the last call's
- * contents; every call rewrites what it needs and resets its counters, but
- * calls whose work overlaps on the GPU (different streams, or a call enqueued
- * before the previous one has finished on another stream) race on it. */
+ * grids' arrays are the caller's, as usual, and must be on the current device,
+ * as must cuda_stream (else STENCIL_EINVAL). The call is synchronous: it
+ * uploads the plan (waiting for cuda_stream), enqueues the launch on
+ * cuda_stream and updates the grids' parities; if status_out is not NULL it
+ * also waits for the launch and stores STENCIL_OK or STENCIL_ETIMEOUT there.
+ * It must never be called on a stream that is capturing a CUDA graph (it
+ * returns STENCIL_EINVAL there without touching the capture).
+ * Every call looks up the array's device address on the current device.
+ * All calls share the one array and it keeps the last call's contents; every
+ * call rewrites what it needs and resets its counters, but calls whose work
+ * overlaps on the GPU (different streams, or a call enqueued before the
+ * previous one has finished on another stream) race on it, and so do calls
+ * made at the same time from several host threads, even on one stream (one
+ * call's upload can land between another's upload and its launch): callers
+ * must serialise their calls. */
 int stencil_batch_run_noalloc(const stencil_t* grids, const int* T, int n, const stencil_tuning* tuning,
                               void* cuda_stream, int* status_out);
 
@@ -285,7 +314,8 @@ int stencil_batch_run_noalloc(const stencil_t* grids, const int* T, int n, const
  * previous stream is the caller's (events). */
 int stencil_set_stream(stencil_t h, void* cuda_stream);
 
-/* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error. */
+/* Wait for the handle's stream; returns STENCIL_ECUDA on an asynchronous error
+ * and STENCIL_ETIMEOUT when the status word is set (as stencil_status). */
 int stencil_sync(stencil_t h);
 
 /* Static description of a status code. */

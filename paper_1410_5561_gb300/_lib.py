@@ -81,6 +81,9 @@ SIGNATURES = [
                                        _P, ctypes.POINTER(_I)]),
     ("stencil_set_stream", _I, [_H, _P]),
     ("stencil_sync", _I, [_H]),
+    ("stencil_status", _I, [_H]),
+    ("stencil_set_wait_limit", _I, [_H, ctypes.c_uint]),
+    ("stencil_inject_stall", _I, [_H, _I]),
     ("stencil_strerror", ctypes.c_char_p, [_I]),
     ("stencil_destroy", _I, [_H]),
 ]

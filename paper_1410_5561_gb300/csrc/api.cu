@@ -26,8 +26,9 @@ struct stencil_grid {
     BlockedTune tune;
     bool tune_set;
     long long launches;
-    long long plan_key;  // persistent blocked plan currently in the workspace (-1: none)
     bool halo_ok;        // both bound field arrays hold `halo` in every non-interior cell
+    bool status_armed;   // the workspace's status word has been zeroed since bind / set_field
+    PersistCtl ctl;      // dependency-wait limit and stall hook of the persistent schedule
 };
 
 static int from_cuda(cudaError_t e) { return e == cudaSuccess ? STENCIL_OK : STENCIL_ECUDA; }
@@ -145,8 +146,10 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
     h->scheme = STENCIL_PLAIN;
     h->tune_set = false;
     h->launches = 0;
-    h->plan_key = -1;
     h->halo_ok = false;
+    h->status_armed = false;
+    h->ctl.spin_limit = 1u << 24;
+    h->ctl.stall_item = -1;
     *out = h;
     return STENCIL_OK;
 }
@@ -184,8 +187,8 @@ int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, v
     for (int m = 0; m < 13; ++m) h->coef[m] = m < nc ? coef[m] : nullptr;
     if (workspace && !aligned16(workspace)) return STENCIL_EINVAL;
     h->ws = workspace;
-    h->plan_key = -1;
     h->halo_ok = false;
+    h->status_armed = false;
     h->bound = true;
     return STENCIL_OK;
 }
@@ -276,6 +279,7 @@ int stencil_set_field(stencil_t h, const void* src, double halo_value, int where
     h->halo = halo_value;
     h->halo_ok = true;
     h->parity = 0;
+    h->status_armed = false;  // a new field: earlier timeouts no longer apply
     return STENCIL_OK;
 }
 
@@ -322,10 +326,16 @@ int stencil_run(stencil_t h, int T) {
     if (h->scheme == STENCIL_BLOCKED) {
         cudaError_t e = cudaErrorNotReady;
         if (h->ws) {
-            // one persistent launch; if the workspace cannot hold the plan for T steps,
+            if (!h->status_armed) {
+                if (cudaMemsetAsync(static_cast<int*>(h->ws) + PERSIST_WS_STATUS, 0, sizeof(int), h->stream) !=
+                    cudaSuccess)
+                    return STENCIL_ECUDA;
+                h->status_armed = true;
+            }
+            // one persistent launch; if the plan for T steps does not fit one launch,
             // run the steps in two parts
-            e = blocked_run_persistent(a, h->field, h->parity, T, h->tune, h->ws, GRID_WORKSPACE_BYTES, h->stream,
-                                       &h->launches, &h->plan_key);
+            e = blocked_run_persistent(a, h->field, h->parity, T, h->tune, h->ws, GRID_WORKSPACE_BYTES, h->ctl,
+                                       h->stream, &h->launches);
             if (e == cudaErrorNotReady && T > 1) {
                 int rc = stencil_run(h, T / 2);
                 if (rc != STENCIL_OK) return rc;
@@ -514,6 +524,9 @@ int stencil_batch_item_count(stencil_batch_t b) { return b ? b->bl.nitems : STEN
 
 int stencil_batch_bind(stencil_batch_t b, void* workspace, void* cuda_stream) {
     if (!b || !workspace || !aligned16(workspace)) return STENCIL_EINVAL;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cap) != cudaSuccess) return STENCIL_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return STENCIL_EINVAL;  // the upload waits for the stream
     std::vector<BatchGrid> g;
     batch_grids(b, g);
     b->stream = static_cast<cudaStream_t>(cuda_stream);
@@ -585,9 +598,38 @@ int stencil_set_stream(stencil_t h, void* cuda_stream) {
     return STENCIL_OK;
 }
 
+// The persistent schedule's status word (synchronous): STENCIL_OK or STENCIL_ETIMEOUT.
+static int read_status(stencil_t h) {
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return STENCIL_ECUDA;
+    if (!h->bound || !h->ws || !h->status_armed) return STENCIL_OK;
+    int v = 0;
+    if (cudaMemcpyAsync(&v, static_cast<int*>(h->ws) + PERSIST_WS_STATUS, sizeof(int), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+        return STENCIL_ECUDA;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return STENCIL_ECUDA;
+    return v == 0 ? STENCIL_OK : STENCIL_ETIMEOUT;
+}
+
 int stencil_sync(stencil_t h) {
     if (!h) return STENCIL_EINVAL;
-    return from_cuda(cudaStreamSynchronize(h->stream));
+    return read_status(h);
+}
+
+int stencil_status(stencil_t h) {
+    if (!h) return STENCIL_EINVAL;
+    return read_status(h);
+}
+
+int stencil_set_wait_limit(stencil_t h, unsigned spins) {
+    if (!h || spins == 0) return STENCIL_EINVAL;
+    h->ctl.spin_limit = spins;
+    return STENCIL_OK;
+}
+
+int stencil_inject_stall(stencil_t h, int tile) {
+    if (!h || tile < -1) return STENCIL_EINVAL;
+    h->ctl.stall_item = tile;
+    return STENCIL_OK;
 }
 
 const char* stencil_strerror(int status) {

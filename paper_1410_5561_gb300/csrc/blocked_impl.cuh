@@ -943,34 +943,69 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_batch_kernel(const BatchA
 // tiles it depends on have been published by all of their x tiles. Clusters
 // are launched only as many as can be resident, and each walks its tiles in
 // increasing order while depending only on smaller indices, so the smallest
-// unfinished tile can always proceed. A wait that exceeds its limit records
-// the status word and proceeds (the results are then invalid but every CTA of
-// the cluster keeps to the same barriers, so nothing can hang).
+// unfinished tile can always proceed. A wait that exceeds its limit sets the
+// (sticky) status word and proceeds (the results are then invalid but every CTA
+// of the cluster keeps to the same barriers, so nothing can hang).
+//
+// The tile list is not stored: row k of the list holds the diamonds
+// b = bmin[k] .. bmin[k] + (base[k+1] - base[k]) - 1 as tiles base[k] ..
+// base[k+1] - 1, and the table is a __grid_constant__ kernel parameter, so a
+// run needs no host-to-device copy of a plan (it stays asynchronous and can be
+// captured in a CUDA graph).
+constexpr int MAXPROWS = 960;  // diamond rows of one persistent launch (longer runs are split)
+
+struct PlanRows {
+    int nrows, nitems;
+    int bmin[MAXPROWS];
+    int base[MAXPROWS + 1];
+};
+
+// Tile i of the plan: its row k, diamond b and the tiles it waits for.
+__device__ __forceinline__ void plan_tile(const PlanRows& P, int i, int& k, int& b) {
+    int lo = 0, hi = P.nrows - 1;  // the last row whose first tile is <= i (empty rows share a base)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.base[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    k = lo;
+    b = P.bmin[lo] + (i - P.base[lo]);
+}
+__device__ __forceinline__ int plan_index(const PlanRows& P, int k, int b) {
+    if (k < 0 || k >= P.nrows) return -1;
+    const int o = b - P.bmin[k];
+    return (o >= 0 && o < P.base[k + 1] - P.base[k]) ? P.base[k] + o : -1;
+}
+
 template <typename TF, typename TC>
 struct PersistArgs {
     GridArgs<TF, TC> G;
-    const BatchItem* items;
-    int nitems;
-    int* done;    // per item: x tiles finished
-    int* status;  // 0 ok, 1 a dependency wait gave up
+    int* status;      // sticky: 1 once a dependency wait gave up
+    int* never;       // a flag no tile sets (the stall hook waits on it)
+    int* done;        // per tile: x tiles finished
     unsigned spin_limit;
+    int stall_item;   // test hook: this tile also waits on *never (-1: none)
+    PlanRows P;
 };
 
 template <int KIND, typename TF, typename TC, int K, int NF>
-__global__ void __launch_bounds__(BLK_MAXT, 1) blocked_persist_kernel(const PersistArgs<TF, TC> A) {
+__global__ void __launch_bounds__(BLK_MAXT, 1) blocked_persist_kernel(const __grid_constant__ PersistArgs<TF, TC> A) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ TileMeta M;
     TF* ring = reinterpret_cast<TF*>(smem_raw);
     const int CX = A.G.CX;
     const int nclusters = (int)gridDim.y;
-    for (int i = (int)blockIdx.y; i < A.nitems; i += nclusters) {
-        const BatchItem it = A.items[i];
+    for (int i = (int)blockIdx.y; i < A.P.nitems; i += nclusters) {
+        int k, b;
+        plan_tile(A.P, i, k, b);
         if (threadIdx.x == 0) {
-            for (int q = 0; q < 3; ++q) {
-                const int dd = it.dep[q];
-                if (dd < 0) continue;
+            const int dep[4] = {plan_index(A.P, k - 1, b), plan_index(A.P, k - 1, b + 1),
+                                plan_index(A.P, k - 2, b + 1), i == A.stall_item ? -2 : -1};
+            for (int q = 0; q < 4; ++q) {
+                if (dep[q] == -1) continue;
+                const int* flag = dep[q] >= 0 ? A.done + dep[q] : A.never;
                 unsigned n = 0;
-                while (ld_acquire_gpu(A.done + dd) < CX) {
+                while (ld_acquire_gpu(flag) < CX) {
                     if (ld_volatile(A.status) != 0) break;
                     if (++n > A.spin_limit) {
                         atomicCAS(A.status, 0, 1);
@@ -981,7 +1016,7 @@ __global__ void __launch_bounds__(BLK_MAXT, 1) blocked_persist_kernel(const Pers
             }
         }
         __syncthreads();
-        run_tile<KIND, TF, TC, K, NF>(A.G, it.k, it.b, (int)blockIdx.x, CX > 1, A.G.p0, M, ring);
+        run_tile<KIND, TF, TC, K, NF>(A.G, k, b, (int)blockIdx.x, CX > 1, A.G.p0, M, ring);
         __threadfence();  // this thread's HBM stores of the tile are visible GPU-wide
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(A.done + i, 1);
@@ -1448,26 +1483,53 @@ cudaError_t batch_launch(const BatchLaunch& bl, cudaStream_t s) {
 #endif  // STG_BLOCKED_MAIN
 
 
-// Persistent single-grid run: the plan (tile list) lives in the caller's workspace.
-// Returns cudaErrorNotReady when the workspace cannot hold the plan for T steps
-// (the caller then runs T in parts or falls back to row launches).
+// Row table of the persistent single-grid plan (rows whose tiles own no update are
+// empty). false: more rows than one launch can carry.
+static bool plan_rows(const SweepArgs& a, int T, int dw, PlanRows* P) {
+    const int R = kind_radius(a.kind), Ny = a.L.ny;
+    int n = 0, k = 0;
+    for (;; ++k) {
+        int tlo, thi;
+        row_trange(dw, R, T, k, tlo, thi);
+        if (tlo >= T) break;
+        if (k >= MAXPROWS) return false;
+        int bmin = 1 << 30, bmax = -(1 << 30);
+        for (int b = -(k + 2) / 2 - 2; b <= (2 * Ny / dw - k) / 2 + 2; ++b) {
+            bool any = false;
+            for (int t = tlo; t < thi && !any; ++t) {
+                int lo, hi;
+                level_rows(dw, R, Ny, b + k, b, t, lo, hi);
+                any = hi > lo;
+            }
+            if (any) {
+                bmin = b < bmin ? b : bmin;
+                bmax = b > bmax ? b : bmax;
+            }
+        }
+        P->base[k] = n;
+        P->bmin[k] = bmax >= bmin ? bmin : 0;
+        if (bmax >= bmin) n += bmax - bmin + 1;
+    }
+    P->nrows = k;
+    P->base[k] = n;
+    P->nitems = n;
+    return true;
+}
+
+// Persistent single-grid run. The workspace holds the status word, the never-set
+// flag and one completion counter per tile (PERSIST_WS_* in internal.h). Returns
+// cudaErrorNotReady when the plan does not fit one launch (more diamond rows than
+// the parameter table holds, or more tiles than the workspace has counters for);
+// the caller then runs T in parts.
 template <int KIND, typename TF, typename TC, int K, int NF>
 static cudaError_t persist_k(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
-                             const BlkShape& sh, void* ws, size_t ws_bytes, cudaStream_t st, long long* launches,
-                             long long* plan_key) {
-    BatchGrid g{};
-    g.a = a;
-    g.field[0] = field[0];
-    g.field[1] = field[1];
-    g.parity = p0;
-    g.T = T;
-    std::vector<BatchItem> items;
-    std::vector<int> ntiles;
-    const int n = batch_items(&g, 1, tn.dw, items, ntiles);
+                             const BlkShape& sh, void* ws, size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st,
+                             long long* launches) {
+    PersistArgs<TF, TC> A{};
+    if (!plan_rows(a, T, tn.dw, &A.P)) return cudaErrorNotReady;
+    const int n = A.P.nitems;
     if (n == 0) return cudaSuccess;
-    const size_t items_bytes = align256(sizeof(BatchItem) * (size_t)n);
-    const size_t need = items_bytes + align256(sizeof(int) * (size_t)(n + 1));
-    if (need > ws_bytes) return cudaErrorNotReady;
+    if (sizeof(int) * ((size_t)PERSIST_WS_DONE + n) > ws_bytes) return cudaErrorNotReady;
     auto kfn = blocked_persist_kernel<KIND, TF, TC, K, NF>;
     cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
     if (e) return e;
@@ -1498,25 +1560,18 @@ static cudaError_t persist_k(const SweepArgs& a, void* const field[2], int p0, i
     }
     if (nclusters < 1) return cudaErrorInvalidConfiguration;
     if (nclusters > n) nclusters = n;
-    char* w = static_cast<char*>(ws);
-    int* done = reinterpret_cast<int*>(w + items_bytes);
-    // the tile list depends only on (T, D_w, shape): upload it once per change
-    const long long key = ((long long)T << 32) ^ ((long long)tn.dw << 16) ^ (long long)a.L.ny;
-    if (!plan_key || *plan_key != key) {
-        if ((e = cudaMemcpyAsync(w, items.data(), sizeof(BatchItem) * (size_t)n, cudaMemcpyHostToDevice, st)))
-            return e;
-        if ((e = cudaStreamSynchronize(st))) return e;  // the host copy of the plan goes out of scope
-        if (plan_key) *plan_key = key;
-    }
-    if ((e = cudaMemsetAsync(done, 0, sizeof(int) * (size_t)(n + 1), st))) return e;
-    PersistArgs<TF, TC> A{};
+    int* w = static_cast<int*>(ws);
+    // the never-set flag and the completion counters start at 0; the status word is kept
+    if ((e = cudaMemsetAsync(w + PERSIST_WS_NEVER, 0, sizeof(int) * (size_t)(PERSIST_WS_DONE - PERSIST_WS_NEVER + n),
+                             st)))
+        return e;
     A.G = grid_args<TF, TC>(a, field, p0, T, tn, sh);
     A.G.CX = nxt;
-    A.items = reinterpret_cast<const BatchItem*>(w);
-    A.nitems = n;
-    A.done = done;
-    A.status = done + n;
-    A.spin_limit = 1u << 24;
+    A.status = w + PERSIST_WS_STATUS;
+    A.never = w + PERSIST_WS_NEVER;
+    A.done = w + PERSIST_WS_DONE;
+    A.spin_limit = ctl.spin_limit;
+    A.stall_item = ctl.stall_item;
     cfg.gridDim = dim3((unsigned)nxt, (unsigned)nclusters, 1);
     cfg.numAttrs = nxt > 1 ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, kfn, A);
@@ -1526,12 +1581,13 @@ static cudaError_t persist_k(const SweepArgs& a, void* const field[2], int p0, i
 }
 
 template <int KIND, typename TF, typename TC>
-cudaError_t persist_t(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
-                             void* ws, size_t ws_bytes, cudaStream_t st, long long* launches, long long* pk) {
+cudaError_t persist_t(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn, void* ws,
+                      size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     BlkShape sh = blk_shape(a, tn);
     if (!sh.ok) return cudaErrorInvalidValue;
 #define STG_PER(KK, NFF) \
-    if (sh.K == KK && tn.nf == NFF) return persist_k<KIND, TF, TC, KK, NFF>(a, field, p0, T, tn, sh, ws, ws_bytes, st, launches, pk);
+    if (sh.K == KK && tn.nf == NFF) \
+        return persist_k<KIND, TF, TC, KK, NFF>(a, field, p0, T, tn, sh, ws, ws_bytes, ctl, st, launches);
     STG_PER(1, 1) STG_PER(2, 1) STG_PER(4, 1) STG_PER(1, 2) STG_PER(2, 2) STG_PER(4, 2)
 #undef STG_PER
     return cudaErrorInvalidValue;
@@ -1539,26 +1595,27 @@ cudaError_t persist_t(const SweepArgs& a, void* const field[2], int p0, int T, c
 
 #ifdef STG_BLOCKED_MAIN
 cudaError_t blocked_run_persistent(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn,
-                                   void* ws, size_t ws_bytes, cudaStream_t s, long long* launches, long long* pk) {
+                                   void* ws, size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s,
+                                   long long* launches) {
     if (T <= 0 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
     switch (a.kind) {
         case K7C:
-            if (a.fdt == DT_F32) return persist_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
-            if (a.fdt == DT_F64) return persist_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+            if (a.fdt == DT_F32) return persist_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F64) return persist_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
             break;
         case K7V:
             if (a.fdt == DT_F32 && a.cdt == DT_F32)
-                return persist_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+                return persist_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return persist_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
-            if (a.fdt == DT_F64) return persist_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+                return persist_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F64) return persist_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
             break;
         case K25V:
             if (a.fdt == DT_F32 && a.cdt == DT_F32)
-                return persist_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+                return persist_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return persist_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
-            if (a.fdt == DT_F64) return persist_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, s, launches, pk);
+                return persist_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F64) return persist_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
             break;
     }
     return cudaErrorInvalidValue;

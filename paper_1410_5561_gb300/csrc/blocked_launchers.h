@@ -13,7 +13,7 @@ template <int KIND, typename TF, typename TC>
 cudaError_t batch_launch_t(const BatchLaunch& bl, cudaStream_t s);
 template <int KIND, typename TF, typename TC>
 cudaError_t persist_t(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tn, void* ws,
-                      size_t ws_bytes, cudaStream_t st, long long* launches, long long* pk);
+                      size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches);
 
 }  // namespace stg
 
@@ -25,8 +25,8 @@ cudaError_t persist_t(const SweepArgs& a, void* const field[2], int p0, int T, c
                                                             const BlockedTune&, cudaStream_t, long long*);  \
     PREFIX template cudaError_t batch_launch_t<KIND, TF, TC>(const BatchLaunch&, cudaStream_t);              \
     PREFIX template cudaError_t persist_t<KIND, TF, TC>(const SweepArgs&, void* const[2], int, int,          \
-                                                       const BlockedTune&, void*, size_t, cudaStream_t,      \
-                                                       long long*, long long*);
+                                                       const BlockedTune&, void*, size_t, const PersistCtl&, \
+                                                       cudaStream_t, long long*);
 
 // The (kind, field, coefficient) combinations the library supports.
 #define STG_BLOCKED_FOR_EACH_7C(M, P) M(P, K7C, float, float) M(P, K7C, double, double)

@@ -57,11 +57,23 @@ cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, const void* u, 
 // dst = src on the interior, 0 on every other cell (FP32 / FP64).
 cudaError_t copy_interior_zero_halo(const Layout& L, int dt, const void* src, void* dst, cudaStream_t s);
 
+// Controls of a persistent single-grid launch.
+struct PersistCtl {
+    unsigned spin_limit;  // bound on the spin iterations of one dependency wait
+    int stall_item;       // test hook: tile that also waits on a flag no tile sets (-1: none)
+};
+// Words (ints) of a grid workspace used by the persistent schedule: the status word
+// (sticky: set to 1 when a dependency wait gives up), a flag no tile ever sets, then
+// one completion counter per tile.
+constexpr int PERSIST_WS_STATUS = 0, PERSIST_WS_NEVER = 1, PERSIST_WS_DONE = 2;
+
 // Blocked run of T steps by one persistent launch whose clusters walk the
-// dependency-ordered tile list (plan kept in ws). cudaErrorNotReady: ws too small
-// for T. plan_key caches the uploaded plan (reset it when ws changes).
+// dependency-ordered tile list (derived on the device from a row table passed as a
+// kernel parameter; ws holds only the status word and the counters).
+// cudaErrorNotReady: the plan for T steps does not fit one launch.
 cudaError_t blocked_run_persistent(const SweepArgs& a, void* const field[2], int p0, int T, const BlockedTune& tune,
-                                   void* ws, size_t ws_bytes, cudaStream_t s, long long* launches, long long* plan_key);
+                                   void* ws, size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s,
+                                   long long* launches);
 
 // Workspace a grid handle asks for: room for the persistent blocked plan.
 constexpr size_t GRID_WORKSPACE_BYTES = size_t(4) << 20;

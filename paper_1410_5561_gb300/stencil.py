@@ -179,6 +179,24 @@ class Stencil:
     def run(self, T: int):
         C.call("stencil_run", self._h, int(T))
 
+    def capture(self, T: int) -> torch.cuda.CUDAGraph:
+        """A CUDA graph holding stencil_run(T) (not executed by capturing). Each replay
+        advances the field by T steps from the array that was current at capture time, so
+        replays chain when T is even; the handle's parity is left as before capturing."""
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(self.stream)
+        old, par = self.stream, self.parity
+        self.set_stream(side)
+        try:
+            with torch.cuda.graph(g, stream=side):
+                self.run(T)
+        finally:
+            self.set_stream(old)
+        if self.parity != par:
+            raise RuntimeError("capture of an odd step count: replays would not chain")
+        return g
+
     # ------------------------------------------------------------ adjoint
     def adjoint_workspace(self, T: int, ckpt_every: int = 0) -> torch.Tensor:
         """Device workspace for run_checkpointed / run_adjoint (reused when large enough)."""
@@ -230,7 +248,21 @@ class Stencil:
         return int(n.value)
 
     def sync(self):
+        """Wait for the grid's stream; raises on a CUDA error or a device-side timeout."""
         C.call("stencil_sync", self._h)
+
+    def status(self) -> int:
+        """The device error/timeout word (waits for the stream): 0, or a negative status."""
+        return int(C.lib().stencil_status(self._h))
+
+    def set_wait_limit(self, spins: int):
+        """Bound on the spin iterations of one dependency wait of the persistent schedule."""
+        C.call("stencil_set_wait_limit", self._h, ctypes.c_uint(int(spins)))
+
+    def inject_stall(self, tile: int):
+        """Test hook: tile ``tile`` of later persistent launches waits on a flag no tile sets
+        (-1 removes it)."""
+        C.call("stencil_inject_stall", self._h, int(tile))
 
     def close(self):
         if getattr(self, "_h", None):

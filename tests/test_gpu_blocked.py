@@ -176,3 +176,58 @@ def test_auto_scheme_and_default_tuning():
         d.set_tuning("blocked")  # library default tuning
         d.run(9)
         assert np.array_equal(d.get_field().cpu().numpy(), _run(p, 9, "plain")), (kind, fdt)
+
+
+def test_persistent_timeout_is_reported_not_hung():
+    """A dependency wait of the single-grid persistent launch that runs out (a tile made to
+    wait on a flag no tile sets, with a short limit) ends the launch with the status word
+    set: stencil_status and stencil_sync report STENCIL_ETIMEOUT instead of returning
+    invalid data silently. A new field clears it, and the next run is exact again."""
+    from paper_1410_5561_gb300._lib import STATUS, StencilError
+    p = Problem("7pt_const", 70, 64, 24, fdt="f32", seed=18)
+    s = p.make()
+    s.set_tuning("blocked", Tuning(8, 1, 8, 16))
+    s.run(5)
+    assert s.status() == 0
+    s.set_wait_limit(2000)
+    s.inject_stall(7)
+    s.run(13)
+    assert STATUS[s.status()] == "STENCIL_ETIMEOUT"
+    with pytest.raises(StencilError):
+        s.sync()
+    s.inject_stall(-1)
+    s.set_wait_limit(1 << 24)
+    u0, _ = p.torch_inputs("cuda")
+    s.set_field(u0, halo=p.halo)
+    assert s.status() == 0
+    s.run(13)
+    s.sync()
+    assert s.status() == 0
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 13, "plain"))
+    s.inject_stall(1 << 30)  # beyond the plan: no effect
+    s.set_field(u0, halo=p.halo)
+    s.run(13)
+    assert s.status() == 0
+
+
+@pytest.mark.parametrize("kind,fdt,cdt,tn", [
+    ("7pt_const", "f32", None, Tuning(8, 2, 16, 16)),
+    ("7pt_var", "f32", "bf16", Tuning(8, 1, 8, 16)),
+    ("25pt_var", "f32", None, Tuning(16, 1, 8, 12)),
+])
+def test_persistent_run_captured_in_a_cuda_graph(kind, fdt, cdt, tn):
+    """stencil_run of the persistent blocked schedule enqueues kernels and memsets only (no
+    host copy of a plan, no wait), so it can be captured; two replays of run(6) give the
+    plain sweep's 12 steps bit for bit."""
+    import torch
+    p = Problem(kind, 41, 37, 19, fdt=fdt, cdt=cdt, seed=19, halo=0.25)
+    s = p.make()
+    s.set_tuning("blocked", tn)
+    s.run(2)  # first run after set_field (status word reset) outside the graph
+    torch.cuda.synchronize()
+    g = s.capture(6)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 14, "plain"))

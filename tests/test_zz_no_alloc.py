@@ -6,7 +6,8 @@ a latency-critical loop because it can synchronise the device); it keeps the
 batch's scratch in a fixed array owned by the library. These tests call it
 through the C ABI and compare its grids, bit for bit (the tolerance every
 blocked and batched test uses), with the workspace-based batch path, over two
-calls in a row. This file is collected last on purpose.
+calls in a row. This file is collected last on purpose: if it fails, a run that
+stops at the first failure has already run every other test.
 """
 import ctypes
 
@@ -62,6 +63,14 @@ def test_noalloc_batch_rejects_a_plan_beyond_its_scratch():
     before = [g.get_field().cpu().numpy() for g in grids]
     ts = (ctypes.c_int * 2)(200, 200)
     t = Tuning(2, 1, 16, 0).c()
+    # the same batch is valid for the workspace path, and needs more than the 4 MiB scratch:
+    # the size limit, not the tuning or the grids, is what rejects the allocation-free call
+    b = ctypes.c_void_p()
+    C.call("stencil_batch_create", ctypes.byref(b), _handles(grids), ts, 2, ctypes.byref(t))
+    try:
+        assert int(C.lib().stencil_batch_workspace_bytes(b)) > (4 << 20)
+    finally:
+        C.lib().stencil_batch_destroy(b)
     status = ctypes.c_int(-99)
     rc = C.lib().stencil_batch_run_noalloc(_handles(grids), ts, 2, ctypes.byref(t),
                                            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),

@@ -49,7 +49,7 @@ typedef struct stencil_grid* stencil_t; /* opaque, owned by the library */
 
 enum stencil_kind { STENCIL_7PT_CONST = 0, STENCIL_7PT_VAR = 1, STENCIL_25PT_VAR = 2 };
 enum stencil_dtype { STENCIL_F32 = 0, STENCIL_F64 = 1, STENCIL_BF16 = 2 };
-enum stencil_scheme { STENCIL_PLAIN = 0, STENCIL_BLOCKED = 1, STENCIL_AUTO = 2 };
+enum stencil_scheme { STENCIL_PLAIN = 0, STENCIL_BLOCKED = 1, STENCIL_AUTO = 2, STENCIL_WAVEFRONT = 3 };
 /* Where a dense array passed to set_coeffs / set_field / get_field lives.
  * STENCIL_HOST: host memory; the call waits for its copy when the caller needs
  * the data back (page-locked memory is moved by the library's copy kernel,
@@ -143,6 +143,14 @@ int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* ar
 int stencil_set_field(stencil_t h, const void* src, double halo_value, int where);
 
 /* Select the schedule used by run(): STENCIL_PLAIN (one launch per step),
+ * STENCIL_WAVEFRONT (wavefront temporal blocking through L2: Section II-A's
+ * thread group sharing one cache block, here every CTA of the GPU sharing the
+ * L2; each launch advances h = dw / (2R) steps: time level l of the pass
+ * sweeps z chunks of nf planes (nf >= R) two chunks behind level l-1, on xy
+ * tiles of 32 vectors by `warps` rows (4, 8 or 16, >= R), the CTAs waiting on
+ * bounded completion flags; xtile is ignored; NULL: h = 2, 8-plane chunks, 8
+ * rows; needs a bound workspace, else STENCIL_EINVAL; bit-identical to the
+ * plain sweep), or
  * STENCIL_BLOCKED with *tuning (NULL: library default: D_w = 8R, N_F = 2 where it
  * fits, 16 warps for R = 1, the widest x tile whose rows fit one warp of vectors), or
  * STENCIL_AUTO (plain for FP64 fields and the 25-point stencil, where the plain sweep

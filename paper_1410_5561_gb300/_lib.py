@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libstencil_gb300.so")
 
 STENCIL_7PT_CONST, STENCIL_7PT_VAR, STENCIL_25PT_VAR = 0, 1, 2
 STENCIL_F32, STENCIL_F64, STENCIL_BF16 = 0, 1, 2
-STENCIL_PLAIN, STENCIL_BLOCKED, STENCIL_AUTO = 0, 1, 2
+STENCIL_PLAIN, STENCIL_BLOCKED, STENCIL_AUTO, STENCIL_WAVEFRONT = 0, 1, 2, 3
 STENCIL_HOST, STENCIL_DEVICE, STENCIL_HOST_ASYNC = 0, 1, 2
 STENCIL_FIELD_ARRAY, STENCIL_COEF_ARRAY, STENCIL_GRAD_ARRAY = 0, 1, 2
 

@@ -24,6 +24,7 @@ struct stencil_grid {
     int parity;
     int scheme;
     BlockedTune tune;
+    WaveTune wtune;
     bool tune_set;
     long long launches;
     bool halo_ok;        // both bound field arrays hold `halo` in every non-interior cell
@@ -289,6 +290,22 @@ int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning) {
         h->scheme = STENCIL_PLAIN;
         return STENCIL_OK;
     }
+    if (scheme == STENCIL_WAVEFRONT) {
+        const int R = kind_radius(h->kind);
+        WaveTune w{2, R > 8 ? R : 8, 8, 2};  // default: two levels per pass, 8-plane chunks, 8-row tiles
+        if (tuning) {
+            if (tuning->dw < 2 * R || tuning->dw % (2 * R) != 0) return STENCIL_EINVAL;
+            w.h = tuning->dw / (2 * R);
+            w.zc = tuning->nf;
+            w.by = tuning->warps;
+        }
+        const size_t need = wave_workspace_bytes(args_of(h), w);
+        if (need == 0) return STENCIL_EINVAL;
+        if (!h->ws || need > GRID_WORKSPACE_BYTES) return STENCIL_EINVAL;
+        h->scheme = STENCIL_WAVEFRONT;
+        h->wtune = w;
+        return STENCIL_OK;
+    }
     if (scheme != STENCIL_BLOCKED && scheme != STENCIL_AUTO) return STENCIL_EINVAL;
     if (scheme == STENCIL_AUTO && (h->fdt == DT_F64 || h->kind == STENCIL_25PT_VAR)) {
         // Measured on GB300: FP64 sweeps are bound by the FP64 units (1/60 of the FP32 rate),
@@ -323,15 +340,19 @@ int stencil_run(stencil_t h, int T) {
     if (!h->bound) return STENCIL_EUNBOUND;
     if (T == 0) return STENCIL_OK;
     SweepArgs a = args_of(h);
-    if (h->scheme == STENCIL_BLOCKED) {
+    if ((h->scheme == STENCIL_BLOCKED || h->scheme == STENCIL_WAVEFRONT) && h->ws && !h->status_armed) {
+        if (cudaMemsetAsync(static_cast<int*>(h->ws) + PERSIST_WS_STATUS, 0, sizeof(int), h->stream) != cudaSuccess)
+            return STENCIL_ECUDA;
+        h->status_armed = true;
+    }
+    if (h->scheme == STENCIL_WAVEFRONT) {
+        cudaError_t e = wave_run(a, h->field, h->parity, T, h->wtune, h->ws, GRID_WORKSPACE_BYTES, h->ctl, h->stream,
+                                 &h->launches);
+        if (e == cudaErrorInvalidValue) return STENCIL_EINVAL;
+        if (e != cudaSuccess) return STENCIL_ECUDA;
+    } else if (h->scheme == STENCIL_BLOCKED) {
         cudaError_t e = cudaErrorNotReady;
         if (h->ws) {
-            if (!h->status_armed) {
-                if (cudaMemsetAsync(static_cast<int*>(h->ws) + PERSIST_WS_STATUS, 0, sizeof(int), h->stream) !=
-                    cudaSuccess)
-                    return STENCIL_ECUDA;
-                h->status_armed = true;
-            }
             // one persistent launch; if the plan for T steps does not fit one launch,
             // run the steps in two parts
             e = blocked_run_persistent(a, h->field, h->parity, T, h->tune, h->ws, GRID_WORKSPACE_BYTES, h->ctl,

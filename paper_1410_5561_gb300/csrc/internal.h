@@ -75,8 +75,25 @@ cudaError_t blocked_run_persistent(const SweepArgs& a, void* const field[2], int
                                    void* ws, size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s,
                                    long long* launches);
 
-// Workspace a grid handle asks for: room for the persistent blocked plan.
-constexpr size_t GRID_WORKSPACE_BYTES = size_t(4) << 20;
+// Workspace a grid handle asks for: the persistent schedules' status word and
+// completion counters.
+constexpr size_t GRID_WORKSPACE_BYTES = size_t(16) << 20;
+
+// Wavefront schedule through L2 (wavefront.cu): h time levels per pass, z chunks of
+// zc planes, xy tiles of 32 vectors by `by` rows (one CTA), level l trailing level
+// l-1 by `lag` chunks.
+struct WaveTune {
+    int h, zc, by, lag;
+};
+// Workspace words (ints) of the wavefront schedule: the status word (shared with the
+// persistent blocked schedule), a flag no unit sets, the unit counter, then one
+// completion flag per unit.
+constexpr int WAVE_WS_STATUS = 0, WAVE_WS_NEVER = 1, WAVE_WS_HEAD = 2, WAVE_WS_FLAGS = 3;
+// Workspace bytes one pass of h levels needs (0 if the tuning is malformed for the grid).
+size_t wave_workspace_bytes(const SweepArgs& a, const WaveTune& tn);
+// T steps in passes of tn.h levels, one launch per pass.
+cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
+                     size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches);
 
 // Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);

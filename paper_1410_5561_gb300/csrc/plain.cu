@@ -4,23 +4,16 @@
 //
 // Thread mapping: a warp covers 32 vectors of V = 16/sizeof(field) consecutive
 // x values (128-bit accesses); a CTA stacks BY warps along y; each thread walks
-// a chunk of z planes and keeps the 2R+1 planes of its own column in a
-// register ring, so each z-neighbour is loaded once, plus PF planes loaded
-// ahead so that several HBM loads per thread are in flight. x- and
-// y-neighbours are plain aligned vector loads that hit L1/L2 (they are re-read
-// by the neighbouring threads); coefficients stream through with evict-first
-// loads. The number of z chunks is chosen from the kernel's occupancy so that
-// the CTAs fill whole waves of the GPU.
+// a chunk of z planes (sweep_column.cuh: register ring of the column's planes,
+// neighbours through L1/L2, coefficients with evict-first loads). The number
+// of z chunks is chosen from the kernel's occupancy so that the CTAs fill
+// whole waves of the GPU.
 #include <mutex>
 
 #include "internal.h"
+#include "sweep_column.cuh"
 
 namespace stg {
-
-template <typename TC>
-struct CoefPtrs {
-    const TC* c[13];
-};
 
 // Per stencil and element types: planes loaded ahead (PF) and the CTAs per SM the register
 // allocation must allow (MINB), chosen by measurement on GB300. The constant-coefficient
@@ -39,95 +32,14 @@ template <int KIND, typename TF, typename TC, int BY, int PF>
 __global__ void __launch_bounds__(32 * BY, (PlainCfg<KIND, TF, TC>::MINB))
 plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, CoefPtrs<TC> C,
                    TF c0, TF c1, int zchunk) {
-    constexpr int R = KindTraits<KIND>::R;
-    constexpr int NC = KindTraits<KIND>::NC;
     constexpr int V = 16 / sizeof(TF);
-    constexpr int J = (R + V - 1) / V;  // neighbour vectors needed on each side along x
     const int i0 = (blockIdx.x * 32 + threadIdx.x) * V;
     const int j = blockIdx.y * BY + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
     const int k0 = blockIdx.z * zchunk;
     const int k1 = min(L.nz, k0 + zchunk);
     if (k0 >= k1) return;
-    const size_t sy = (size_t)L.px;
-    const size_t sz = L.plane();
-    size_t base = L.at(i0, j, k0);
-
-    Vec<TF, V> ring[2 * R + 1];  // planes k-R .. k+R of this thread's column
-#pragma unroll
-    for (int r = 0; r < 2 * R; ++r) ring[r] = ldv<TF, V>(src + base + (ptrdiff_t)(r - R) * (ptrdiff_t)sz);
-    Vec<TF, V> ahead[PF > 0 ? PF : 1];  // planes k+R .. k+R+PF-1 (loaded while k - 1 computes)
-#pragma unroll
-    for (int p = 0; p < PF; ++p)
-        if (k0 + p < k1) ahead[p] = ldv<TF, V>(src + base + (size_t)(R + p) * sz);
-
-    for (int k = k0; k < k1; ++k, base += sz) {
-        if constexpr (PF > 0) {
-            ring[2 * R] = ahead[0];
-#pragma unroll
-            for (int p = 0; p + 1 < PF; ++p) ahead[p] = ahead[p + 1];
-            // plane k+R+PF exists (interior or upper halo) while k + PF <= nz - 1
-            if (k + PF < k1) ahead[PF - 1] = ldv<TF, V>(src + base + (size_t)(R + PF) * sz);
-        } else {
-            ring[2 * R] = ldv<TF, V>(src + base + (size_t)R * sz);
-        }
-        // x line around the vector: [i0 - J*V, i0 + (J+1)*V)
-        TF xl[(2 * J + 1) * V];
-#pragma unroll
-        for (int q = -J; q <= J; ++q) {
-            Vec<TF, V> w = (q == 0) ? ring[R] : ldv<TF, V>(src + base + (ptrdiff_t)q * V);
-#pragma unroll
-            for (int e = 0; e < V; ++e) xl[(q + J) * V + e] = w.v[e];
-        }
-        Vec<TF, V> yp[R], ym[R];
-#pragma unroll
-        for (int r = 1; r <= R; ++r) {
-            yp[r - 1] = ldv<TF, V>(src + base + (size_t)r * sy);
-            ym[r - 1] = ldv<TF, V>(src + base - (size_t)r * sy);
-        }
-        Vec<TC, V> cv[NC > 0 ? NC : 1];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) cv[m] = ldv_stream<TC, V>(C.c[m] + base);
-
-        Vec<TF, V> out;
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int xc = J * V + e;
-            if constexpr (KIND == K7C) {
-                out.v[e] = upd7c<TF>(c0, c1, ring[R].v[e], xl[xc + 1], xl[xc - 1], yp[0].v[e],
-                                     ym[0].v[e], ring[R + 1].v[e], ring[R - 1].v[e]);
-            } else if constexpr (KIND == K7V) {
-                TF c[7];
-#pragma unroll
-                for (int m = 0; m < 7; ++m) c[m] = Cvt<TF, TC>::f(cv[m].v[e]);
-                out.v[e] = upd7v<TF>(c, ring[R].v[e], xl[xc + 1], xl[xc - 1], yp[0].v[e], ym[0].v[e],
-                                     ring[R + 1].v[e], ring[R - 1].v[e]);
-            } else {
-                TF c[13], xp[4], xm[4], ypp[4], ymm[4], zp[4], zm[4];
-#pragma unroll
-                for (int m = 0; m < 13; ++m) c[m] = Cvt<TF, TC>::f(cv[m].v[e]);
-#pragma unroll
-                for (int d = 0; d < 4; ++d) {
-                    xp[d] = xl[xc + d + 1];
-                    xm[d] = xl[xc - d - 1];
-                    ypp[d] = yp[d].v[e];
-                    ymm[d] = ym[d].v[e];
-                    zp[d] = ring[R + d + 1].v[e];
-                    zm[d] = ring[R - d - 1].v[e];
-                }
-                out.v[e] = upd25v<TF>(c, ring[R].v[e], xp, xm, ypp, ymm, zp, zm);
-            }
-        }
-        if (i0 + V <= L.nx) {
-            stv<TF, V>(dst + base, out);
-        } else {
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                if (i0 + e < L.nx) dst[base + e] = out.v[e];
-        }
-#pragma unroll
-        for (int r = 0; r < 2 * R; ++r) ring[r] = ring[r + 1];
-    }
+    sweep_column<KIND, TF, TC, PF, true>(L, src, dst, C, c0, c1, i0, j, k0, k1);
 }
 
 // Resident CTAs per SM of one kernel instantiation times the SM count, per device

@@ -1,0 +1,281 @@
+// Wavefront temporal blocking through L2: the thread group of Section II-A
+// (several threads sharing one cache block, the paper's nWD variants) spread
+// over the whole GPU, with the 129 MB L2 as the shared cache block.
+//
+// One launch advances the grid by h time steps (a pass). The grid is cut into
+// xy tiles (32 vectors of x by BY rows, one CTA's worth) and z chunks of ZC
+// planes. Unit (l, c, q) computes time level l of the pass (u_{t+l+1} from
+// u_{t+l}) on chunk c of tile q with the plain sweep's column update
+// (sweep_column.cuh), so every value is bit-identical to the plain sweep. Level
+// l trails level l-1 by LAG chunks: the units are listed in wave order
+// w = c + LAG * l (higher levels first within a wave), and a CTA pops the next
+// unit from an atomic counter. Unit (l, c, q) waits (bounded) for the units
+// (l-1, c', q') with c' in c-1..c+1 and q' in the 3 x 3 tiles around q, which
+// wrote every value it reads (R <= ZC and R <= BY) and which have finished
+// reading every cell it overwrites (level l writes the array that holds
+// u_{t+l-1}). Those units have smaller indices, so the smallest unfinished unit
+// can always run: no launch can deadlock, whatever the number of resident CTAs.
+//
+// HBM traffic per pass: u_t and the coefficients read once, u_{t+h} written
+// once; the intermediate levels' values and the coefficient planes are read
+// again from L2 by the next level a few chunks later (written-back
+// intermediates add s_f per level). The L2 holds about (LAG + 1) ZC planes of
+// every array while a pass runs.
+#include "internal.h"
+#include "sweep_column.cuh"
+
+namespace stg {
+
+constexpr int WAVE_MAXW = 1024;  // waves per pass
+
+template <typename TF, typename TC>
+struct WaveArgs {
+    Layout L;
+    TF* f[2];
+    CoefPtrs<TC> C;
+    TF c0, c1;
+    int p0;         // array holding the pass's input u_t
+    int h, lag;     // levels in this pass; chunks between consecutive levels
+    int zc, nch;    // planes per chunk; chunks
+    int ntx, nty;   // xy tiles
+    int nitems;
+    int* status;    // sticky: 1 once a dependency wait gave up
+    int* never;     // a flag no unit sets (the stall hook waits on it)
+    int* head;      // next unit to pop
+    int* flags;     // [h][nch][nty][ntx]: 1 when the unit has finished
+    unsigned spin_limit;
+    int stall_item;
+    int nwaves;
+    int wbase[WAVE_MAXW + 1];  // first unit of each wave
+};
+
+__device__ __forceinline__ int wv_ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void wv_st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// Levels active in wave w: c = w - lag * l in [0, nch).
+__host__ __device__ inline void wave_levels(int w, int h, int lag, int nch, int& lmin, int& lmax) {
+    lmax = w / lag;
+    if (lmax > h - 1) lmax = h - 1;
+    const int d = w - nch + 1;
+    lmin = d <= 0 ? 0 : (d + lag - 1) / lag;
+}
+
+template <int KIND, typename TF, typename TC, int BY, int PF>
+__global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant__ WaveArgs<TF, TC> A) {
+    constexpr int V = 16 / sizeof(TF);
+    __shared__ int s_item[2];
+    const int ntiles = A.ntx * A.nty;
+    if (threadIdx.x == 0 && threadIdx.y == 0) s_item[0] = atomicAdd(A.head, 1);
+    __syncthreads();
+    for (int buf = 0;; buf ^= 1) {
+        const int i = s_item[buf];
+        if (i >= A.nitems) break;
+        // unit i: wave, level, chunk, tile
+        int lo = 0, hi = A.nwaves - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (A.wbase[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        const int w = lo, o = i - A.wbase[lo];
+        int lmin, lmax;
+        wave_levels(w, A.h, A.lag, A.nch, lmin, lmax);
+        const int l = lmax - o / ntiles, q = o % ntiles;
+        const int c = w - A.lag * l;
+        const int qx = q % A.ntx, qy = q / A.ntx;
+        if (threadIdx.y == 0) {
+            // pop the next unit now, so its index is ready when this one ends
+            if (threadIdx.x == 0) s_item[buf ^ 1] = atomicAdd(A.head, 1);
+            // lane d < 27 waits for unit (l-1, c + dc, tile (qx + dx, qy + dy)); lane 27 for the stall hook
+            const int lane = threadIdx.x;
+            const int* flag = nullptr;
+            if (l > 0 && lane < 27) {
+                const int dc = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+                const int cc = c + dc, yy = qy + dy, xx = qx + dx;
+                if (cc >= 0 && cc < A.nch && yy >= 0 && yy < A.nty && xx >= 0 && xx < A.ntx)
+                    flag = A.flags + (((size_t)(l - 1) * A.nch + cc) * A.nty + yy) * A.ntx + xx;
+            }
+            if (lane == 27 && i == A.stall_item) flag = A.never;
+            if (flag) {
+                unsigned n = 0;
+                while (wv_ld_acquire(flag) == 0) {
+                    if (*(volatile const int*)A.status != 0) break;
+                    if (++n > A.spin_limit) {
+                        atomicCAS(A.status, 0, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                __threadfence();  // the values the units published are visible to this SM's loads
+            }
+        }
+        __syncthreads();
+        const int i0 = (qx * 32 + (int)threadIdx.x) * V;
+        const int j = qy * BY + (int)threadIdx.y;
+        const int k0 = c * A.zc;
+        const int k1 = min(A.L.nz, k0 + A.zc);
+        if (i0 < A.L.nx && j < A.L.ny) {
+            const TF* src = A.f[(A.p0 + l) & 1];
+            TF* dst = A.f[(A.p0 + l + 1) & 1];
+            if (l == A.h - 1)  // the last level's coefficients are not read again in this pass
+                sweep_column<KIND, TF, TC, PF, true, true>(A.L, src, dst, A.C, A.c0, A.c1, i0, j, k0, k1);
+            else
+                sweep_column<KIND, TF, TC, PF, false, true>(A.L, src, dst, A.C, A.c0, A.c1, i0, j, k0, k1);
+        }
+        __threadfence();  // this thread's stores of the unit are visible GPU-wide
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            wv_st_release(A.flags + (((size_t)l * A.nch + c) * A.nty + qy) * A.ntx + qx, 1);
+    }
+}
+
+// ------------------------------------------------------------------- host side
+
+template <int KIND, typename TF, typename TC> struct WaveCfg { static constexpr int PF = 1; };
+template <typename TF> struct WaveCfg<K7C, TF, TF> { static constexpr int PF = 3; };
+template <> struct WaveCfg<K25V, float, float> { static constexpr int PF = 0; };
+
+// Geometry of one pass: chunks, tiles, waves and units; false if the tuning is
+// malformed for this grid.
+struct WaveShape {
+    int h, lag, zc, nch, ntx, nty, nwaves, nitems;
+    size_t flag_words;
+};
+
+static bool wave_shape(const SweepArgs& a, int h, int zc, int by, int lag, WaveShape* s) {
+    const int R = kind_radius(a.kind);
+    const int V = 16 / dtype_bytes(a.fdt);
+    if (h < 1 || zc < R || zc < 1 || by < R || lag < 2) return false;
+    if (by != 4 && by != 8 && by != 16) return false;
+    s->h = h;
+    s->lag = lag;
+    s->zc = zc;
+    s->nch = (a.L.nz + zc - 1) / zc;
+    s->ntx = (a.L.nx + 32 * V - 1) / (32 * V);
+    s->nty = (a.L.ny + by - 1) / by;
+    s->nwaves = s->nch + lag * (h - 1);
+    if (s->nwaves > WAVE_MAXW) return false;
+    long long units = (long long)h * s->nch * s->ntx * s->nty;
+    if (units > (1LL << 30)) return false;
+    s->nitems = (int)units;
+    s->flag_words = (size_t)units;
+    return true;
+}
+
+template <int KIND, typename TF, typename TC, int BY>
+static cudaError_t wave_pass(const SweepArgs& a, void* const field[2], int p0, const WaveShape& sh, int* ws,
+                             const PersistCtl& ctl, cudaStream_t st, long long* launches) {
+    constexpr int PF = WaveCfg<KIND, TF, TC>::PF;
+    auto kfn = wave_kernel<KIND, TF, TC, BY, PF>;
+    WaveArgs<TF, TC> A{};
+    A.L = a.L;
+    A.f[0] = static_cast<TF*>(field[0]);
+    A.f[1] = static_cast<TF*>(field[1]);
+    for (int m = 0; m < kind_ncoef(a.kind); ++m) A.C.c[m] = static_cast<const TC*>(a.coef[m]);
+    A.c0 = (TF)a.c0;
+    A.c1 = (TF)a.c1;
+    A.p0 = p0;
+    A.h = sh.h;
+    A.lag = sh.lag;
+    A.zc = sh.zc;
+    A.nch = sh.nch;
+    A.ntx = sh.ntx;
+    A.nty = sh.nty;
+    A.nitems = sh.nitems;
+    A.status = ws + WAVE_WS_STATUS;
+    A.never = ws + WAVE_WS_NEVER;
+    A.head = ws + WAVE_WS_HEAD;
+    A.flags = ws + WAVE_WS_FLAGS;
+    A.spin_limit = ctl.spin_limit;
+    A.stall_item = ctl.stall_item;
+    A.nwaves = sh.nwaves;
+    const int ntiles = sh.ntx * sh.nty;
+    int n = 0;
+    for (int w = 0; w < sh.nwaves; ++w) {
+        A.wbase[w] = n;
+        int lmin, lmax;
+        wave_levels(w, sh.h, sh.lag, sh.nch, lmin, lmax);
+        if (lmax >= lmin) n += (lmax - lmin + 1) * ntiles;
+    }
+    A.wbase[sh.nwaves] = n;
+    if (n != sh.nitems) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, 32 * BY, 0))) return e;
+    long long ctas = (long long)(per > 0 ? per : 1) * sms;
+    if (ctas > sh.nitems) ctas = sh.nitems;
+    // the never-set flag, the unit counter and the completion flags start at 0; the status is kept
+    if ((e = cudaMemsetAsync(ws + WAVE_WS_NEVER, 0, sizeof(int) * (WAVE_WS_FLAGS - WAVE_WS_NEVER + sh.flag_words),
+                             st)))
+        return e;
+    kfn<<<(unsigned)ctas, dim3(32, BY), 0, st>>>(A);
+    if ((e = cudaGetLastError())) return e;
+    if (launches) ++*launches;
+    return cudaSuccess;
+}
+
+template <int KIND, typename TF, typename TC>
+static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
+                              size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
+    int* w = static_cast<int*>(ws);
+    for (int t = 0; t < T;) {
+        const int h = T - t < tn.h ? T - t : tn.h;
+        WaveShape sh{};
+        if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh)) return cudaErrorInvalidValue;
+        if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
+        cudaError_t e = cudaErrorInvalidValue;
+        const int p = (p0 + t) & 1;
+        if (tn.by == 4) e = wave_pass<KIND, TF, TC, 4>(a, field, p, sh, w, ctl, st, launches);
+        else if (tn.by == 8) e = wave_pass<KIND, TF, TC, 8>(a, field, p, sh, w, ctl, st, launches);
+        else if (tn.by == 16) e = wave_pass<KIND, TF, TC, 16>(a, field, p, sh, w, ctl, st, launches);
+        if (e != cudaSuccess) return e;
+        t += h;
+    }
+    return cudaSuccess;
+}
+
+size_t wave_workspace_bytes(const SweepArgs& a, const WaveTune& tn) {
+    WaveShape sh{};
+    if (!wave_shape(a, tn.h, tn.zc, tn.by, tn.lag, &sh)) return 0;
+    return sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words);
+}
+
+cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
+                     size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches) {
+    if (T <= 0 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
+    if (!ws) return cudaErrorInvalidValue;
+    switch (a.kind) {
+        case K7C:
+            if (a.fdt == DT_F32) return wave_run_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F64)
+                return wave_run_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            break;
+        case K7V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32)
+                return wave_run_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
+                return wave_run_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F64)
+                return wave_run_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            break;
+        case K25V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32)
+                return wave_run_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
+                return wave_run_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F64)
+                return wave_run_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace stg

@@ -18,7 +18,8 @@ KINDS = {"7pt_const": C.STENCIL_7PT_CONST, "7pt_var": C.STENCIL_7PT_VAR,
 RADIUS = {C.STENCIL_7PT_CONST: 1, C.STENCIL_7PT_VAR: 1, C.STENCIL_25PT_VAR: 4}
 NCOEF = {C.STENCIL_7PT_CONST: 0, C.STENCIL_7PT_VAR: 7, C.STENCIL_25PT_VAR: 13}
 DTYPES = {torch.float32: C.STENCIL_F32, torch.float64: C.STENCIL_F64, torch.bfloat16: C.STENCIL_BF16}
-SCHEMES = {"plain": C.STENCIL_PLAIN, "blocked": C.STENCIL_BLOCKED, "auto": C.STENCIL_AUTO}
+SCHEMES = {"plain": C.STENCIL_PLAIN, "blocked": C.STENCIL_BLOCKED, "auto": C.STENCIL_AUTO,
+           "wavefront": C.STENCIL_WAVEFRONT}
 
 
 def kind_id(kind) -> int:

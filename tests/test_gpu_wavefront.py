@@ -1,0 +1,132 @@
+"""Wavefront temporal blocking through L2 (STENCIL_WAVEFRONT).
+
+Each unit of the schedule updates its cells with the plain sweep's column code,
+so the result must equal the plain sweep bit for bit on any shape, step count
+and tuning: a missed dependency (a unit reading a neighbour's plane before it
+was written, or overwriting a cell a lower level still reads) shows up as a
+changed bit. Oracle parity is checked as well, and the bounded waits are made to
+run out on purpose (a stall hook) to check that the timeout is reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_5561_gb300.stencil import Tuning
+from tests._util import Problem, step_tol
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(p, T, scheme, tuning=None):
+    s = p.make()
+    s.set_tuning(scheme, tuning)
+    s.run(T)
+    s.sync()
+    return s.get_field().cpu().numpy()
+
+
+# Tuning(D_w = 2R h, z-chunk planes, rows per tile, ignored)
+R1_WAVE = [Tuning(4, 1, 4, 0), Tuning(6, 3, 8, 0), Tuning(8, 2, 16, 0), Tuning(2, 5, 4, 0)]
+R4_WAVE = [Tuning(16, 4, 4, 0), Tuning(24, 5, 8, 0), Tuning(8, 8, 16, 0), Tuning(32, 4, 8, 0)]
+
+
+@pytest.mark.parametrize("tn", R1_WAVE, ids=lambda t: f"dw{t.dw}zc{t.nf}by{t.warps}")
+@pytest.mark.parametrize("kind,shape,fdt,cdt", [
+    ("7pt_const", (150, 37, 23), "f32", None),
+    ("7pt_var", (133, 29, 19), "f32", None),
+    ("7pt_var", (40, 43, 17), "f32", "bf16"),
+    ("7pt_const", (70, 21, 12), "f64", None),
+    ("7pt_var", (33, 19, 14), "f64", None),
+])
+@pytest.mark.parametrize("T", [1, 5, 8])
+def test_wavefront_bitwise_equals_plain_r1(kind, shape, fdt, cdt, tn, T):
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=21, halo=0.125)
+    assert np.array_equal(_run(p, T, "plain"), _run(p, T, "wavefront", tn))
+
+
+@pytest.mark.parametrize("tn", R4_WAVE, ids=lambda t: f"dw{t.dw}zc{t.nf}by{t.warps}")
+@pytest.mark.parametrize("shape,fdt,cdt", [((141, 35, 27), "f32", None), ((38, 25, 30), "f64", None),
+                                           ((27, 33, 19), "f32", "bf16")])
+@pytest.mark.parametrize("T", [1, 3, 9])
+def test_wavefront_bitwise_equals_plain_r4(shape, fdt, cdt, tn, T):
+    p = Problem("25pt_var", *shape, fdt=fdt, cdt=cdt, seed=22, halo=-0.25)
+    assert np.array_equal(_run(p, T, "plain"), _run(p, T, "wavefront", tn))
+
+
+@pytest.mark.parametrize("kind,shape,fdt,cdt,T,tn", [
+    ("25pt_var", (70, 61, 45), "f32", None, 8, Tuning(16, 8, 8, 0)),
+    ("25pt_var", (40, 33, 30), "f32", "bf16", 6, Tuning(24, 4, 8, 0)),
+    ("25pt_var", (26, 31, 23), "f64", None, 5, Tuning(16, 4, 4, 0)),
+    ("7pt_var", (50, 47, 31), "f32", None, 10, Tuning(8, 4, 8, 0)),
+    ("7pt_const", (64, 64, 64), "f64", None, 8, Tuning(4, 8, 8, 0)),
+])
+def test_wavefront_matches_oracle(kind, shape, fdt, cdt, T, tn):
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=23)
+    got = _run(p, T, "wavefront", tn).astype(np.float64)
+    ref = p.oracle(T)
+    assert oracle.step_normalised_l2(got, ref, T) <= step_tol(fdt)
+    assert np.max(np.abs(got - ref)) <= p.elementwise_tol(T)
+
+
+def test_wavefront_degenerate_shapes_and_successive_runs():
+    for shape in [(1, 1, 1), (5, 2, 3), (9, 3, 40), (300, 1, 5), (3, 70, 2)]:
+        p = Problem("25pt_var", *shape, fdt="f32", seed=24, halo=0.5)
+        assert np.array_equal(_run(p, 7, "plain"), _run(p, 7, "wavefront", Tuning(16, 4, 4, 0))), shape
+    p = Problem("7pt_var", 45, 40, 33, fdt="f32", seed=25)
+    s = p.make()
+    s.set_tuning("wavefront", Tuning(6, 2, 8, 0))
+    for T in (3, 4, 0, 6):
+        s.run(T)
+    assert s.parity == 13 % 2
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 13, "plain"))
+
+
+def test_wavefront_rejects_malformed_tunings():
+    from paper_1410_5561_gb300._lib import StencilError
+    s = Problem("25pt_var", 40, 40, 40, fdt="f32", seed=1).make()
+    for tn in [Tuning(12, 4, 8, 0),   # D_w not a multiple of 2R
+               Tuning(16, 3, 8, 0),   # chunk thinner than R
+               Tuning(16, 4, 2, 0),   # tile rows fewer than R
+               Tuning(16, 4, 12, 0)]:  # rows per tile not 4, 8 or 16
+        with pytest.raises(StencilError):
+            s.set_tuning("wavefront", tn)
+    w = Problem("7pt_const", 20, 20, 20, fdt="f32", seed=1).make(workspace=False)
+    with pytest.raises(StencilError):
+        w.set_tuning("wavefront", None)  # needs a workspace
+
+
+def test_wavefront_timeout_is_reported_not_hung():
+    """A unit made to wait on a flag that no unit sets, with a short wait limit, ends the
+    launch with the status word set; a new field clears it and the next run is exact."""
+    from paper_1410_5561_gb300._lib import STATUS, StencilError
+    p = Problem("25pt_var", 60, 40, 36, fdt="f32", seed=26)
+    s = p.make()
+    s.set_tuning("wavefront", Tuning(16, 4, 8, 0))
+    s.set_wait_limit(2000)
+    s.inject_stall(9)
+    s.run(6)
+    assert STATUS[s.status()] == "STENCIL_ETIMEOUT"
+    with pytest.raises(StencilError):
+        s.sync()
+    s.inject_stall(-1)
+    s.set_wait_limit(1 << 24)
+    u0, _ = p.torch_inputs("cuda")
+    s.set_field(u0, halo=p.halo)
+    s.run(6)
+    assert s.status() == 0
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 6, "plain"))
+
+
+def test_wavefront_run_captured_in_a_cuda_graph():
+    import torch
+    p = Problem("25pt_var", 41, 37, 29, fdt="f32", seed=27, halo=0.25)
+    s = p.make()
+    s.set_tuning("wavefront", Tuning(16, 4, 8, 0))
+    s.run(2)
+    torch.cuda.synchronize()
+    g = s.capture(4)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 10, "plain"))

@@ -47,26 +47,37 @@ template <> struct FieldLd<true, double, 2> {
     }
 };
 
-template <int KIND, typename TF, typename TC, int PF, bool COEF_STREAM, bool COHERENT = false>
-__device__ __forceinline__ void sweep_column(const Layout& L, const TF* __restrict__ src, TF* __restrict__ dst,
-                                             const CoefPtrs<TC>& C, TF c0, TF c1, int i0, int j, int k0, int k1) {
-    constexpr int R = KindTraits<KIND>::R;
-    constexpr int NC = KindTraits<KIND>::NC;
-    constexpr int V = 16 / sizeof(TF);
-    constexpr int J = (R + V - 1) / V;  // neighbour vectors needed on each side along x
-    const size_t sy = (size_t)L.px;
-    const size_t sz = L.plane();
-    size_t base = L.at(i0, j, k0);
+// The column walk as a resumable state: begin() loads the planes below the first
+// plane, plane() updates the next plane (planes in increasing order, starting at
+// begin's k0; no plane at or beyond k1 is loaded). Loads reach R + PF planes above
+// the plane being updated.
+template <int KIND, typename TF, typename TC, int PF, bool COEF_STREAM, bool COHERENT>
+struct Column {
+    static constexpr int R = KindTraits<KIND>::R;
+    static constexpr int NC = KindTraits<KIND>::NC;
+    static constexpr int V = 16 / sizeof(TF);
+    static constexpr int J = (R + V - 1) / V;  // neighbour vectors needed on each side along x
+    Vec<TF, V> ring[2 * R + 1];                 // planes k-R .. k+R of this thread's column
+    Vec<TF, V> ahead[PF > 0 ? PF : 1];          // planes k+R .. k+R+PF-1 (loaded while k - 1 computes)
+    size_t base;                                // element index of (i0, j, k)
+    int k1;
 
-    Vec<TF, V> ring[2 * R + 1];  // planes k-R .. k+R of this thread's column
+    __device__ __forceinline__ void begin(const Layout& L, const TF* __restrict__ src, int i0, int j, int k0,
+                                          int k1_) {
+        const size_t sz = L.plane();
+        base = L.at(i0, j, k0);
+        k1 = k1_;
 #pragma unroll
-    for (int r = 0; r < 2 * R; ++r) ring[r] = FieldLd<COHERENT, TF, V>::ld(src + base + (ptrdiff_t)(r - R) * (ptrdiff_t)sz);
-    Vec<TF, V> ahead[PF > 0 ? PF : 1];  // planes k+R .. k+R+PF-1 (loaded while k - 1 computes)
+        for (int r = 0; r < 2 * R; ++r) ring[r] = FieldLd<COHERENT, TF, V>::ld(src + base + (ptrdiff_t)(r - R) * (ptrdiff_t)sz);
 #pragma unroll
-    for (int p = 0; p < PF; ++p)
-        if (k0 + p < k1) ahead[p] = FieldLd<COHERENT, TF, V>::ld(src + base + (size_t)(R + p) * sz);
+        for (int p = 0; p < PF; ++p)
+            if (k0 + p < k1) ahead[p] = FieldLd<COHERENT, TF, V>::ld(src + base + (size_t)(R + p) * sz);
+    }
 
-    for (int k = k0; k < k1; ++k, base += sz) {
+    __device__ __forceinline__ void plane(const Layout& L, const TF* __restrict__ src, TF* __restrict__ dst,
+                                          const CoefPtrs<TC>& C, TF c0, TF c1, int i0, int k) {
+        const size_t sy = (size_t)L.px;
+        const size_t sz = L.plane();
         if constexpr (PF > 0) {
             ring[2 * R] = ahead[0];
 #pragma unroll
@@ -135,7 +146,16 @@ __device__ __forceinline__ void sweep_column(const Layout& L, const TF* __restri
         }
 #pragma unroll
         for (int r = 0; r < 2 * R; ++r) ring[r] = ring[r + 1];
+        base += sz;
     }
+};
+
+template <int KIND, typename TF, typename TC, int PF, bool COEF_STREAM, bool COHERENT = false>
+__device__ __forceinline__ void sweep_column(const Layout& L, const TF* __restrict__ src, TF* __restrict__ dst,
+                                             const CoefPtrs<TC>& C, TF c0, TF c1, int i0, int j, int k0, int k1) {
+    Column<KIND, TF, TC, PF, COEF_STREAM, COHERENT> col;
+    col.begin(L, src, i0, j, k0, k1);
+    for (int k = k0; k < k1; ++k) col.plane(L, src, dst, C, c0, c1, i0, k);
 }
 
 }  // namespace stg

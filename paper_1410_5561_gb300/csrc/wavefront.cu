@@ -49,11 +49,6 @@ struct WaveArgs {
     int wbase[WAVE_MAXW + 1];  // first unit of each wave
 };
 
-__device__ __forceinline__ int wv_ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
 __device__ __forceinline__ void wv_st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
@@ -104,7 +99,7 @@ __global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant_
             if (lane == 27 && i == A.stall_item) flag = A.never;
             if (flag) {
                 unsigned n = 0;
-                while (wv_ld_acquire(flag) == 0) {
+                while (*(volatile const int*)flag == 0) {
                     if (*(volatile const int*)A.status != 0) break;
                     if (++n > A.spin_limit) {
                         atomicCAS(A.status, 0, 1);
@@ -112,8 +107,11 @@ __global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant_
                     }
                     __nanosleep(64);
                 }
-                __threadfence();  // the values the units published are visible to this SM's loads
             }
+            __syncwarp();
+            // one converged fence for the warp: each lane that saw a flag set orders the
+            // values published before it ahead of this SM's loads below
+            if (l > 0 || i == A.stall_item) __threadfence();
         }
         __syncthreads();
         const int i0 = (qx * 32 + (int)threadIdx.x) * V;
@@ -128,11 +126,96 @@ __global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant_
             else
                 sweep_column<KIND, TF, TC, PF, false, true>(A.L, src, dst, A.C, A.c0, A.c1, i0, j, k0, k1);
         }
-        __threadfence();  // this thread's stores of the unit are visible GPU-wide
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0)
+        __syncthreads();  // every thread's stores of the unit precede thread 0's fence and flag
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            __threadfence();
             wv_st_release(A.flags + (((size_t)l * A.nch + c) * A.nty + qy) * A.ntx + qx, 1);
+        }
     }
+}
+
+// Stream form, used when every (level, tile) pair can hold a resident CTA: CTA
+// (l, q) walks all z chunks of level l on tile q in order, keeping its column's
+// plane ring in registers across chunks (no per-chunk warm-up). Before chunk c
+// it waits until the level-(l-1) CTAs of the 3 x 3 tiles around q have finished
+// chunks <= c + 1 (the same dependencies as the unit form) and, to keep the L2
+// band short, until the level-(l+1) CTA of its own tile has finished chunk
+// c - LEAD. Progress counters are monotonic per (level, tile). No wait can
+// deadlock while all CTAs are resident: a CTA at the lowest chunk among those
+// not finished has its lower level at least two chunks ahead or can let it
+// advance, since a lower level may lead by LEAD >= 2 chunks.
+constexpr int WAVE_LEAD = 3;
+
+// All chunks of one (level, tile) stream; COEF_STREAM for the last level, whose
+// coefficient loads are evict-first (no later level of the pass reads them).
+template <int KIND, typename TF, typename TC, int BY, bool COEF_STREAM>
+__device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, int q) {
+    constexpr int V = 16 / sizeof(TF);
+    const int ntiles = A.ntx * A.nty;
+    const int qx = q % A.ntx, qy = q / A.ntx;
+    const int i0 = (qx * 32 + (int)threadIdx.x) * V;
+    const int j = qy * BY + (int)threadIdx.y;
+    const bool act = i0 < A.L.nx && j < A.L.ny;
+    const TF* src = A.f[(A.p0 + l) & 1];
+    TF* dst = A.f[(A.p0 + l + 1) & 1];
+    int* prog = A.flags;  // [h][ntiles]: chunks finished
+    const bool last = l == A.h - 1;
+    Column<KIND, TF, TC, 0, COEF_STREAM, true> col;
+    for (int c = 0; c < A.nch; ++c) {
+        if (threadIdx.y == 0) {
+            const int lane = threadIdx.x;
+            const int* flag = nullptr;
+            int need = 0;
+            if (l > 0 && lane < 9) {  // level l-1 of the 3 x 3 tiles: chunks <= c + 1 finished
+                const int yy = qy + lane / 3 - 1, xx = qx + lane % 3 - 1;
+                if (yy >= 0 && yy < A.nty && xx >= 0 && xx < A.ntx) {
+                    flag = prog + (size_t)(l - 1) * ntiles + (size_t)yy * A.ntx + xx;
+                    need = c + 2 < A.nch ? c + 2 : A.nch;
+                }
+            }
+            if (lane == 9 && !last && c - WAVE_LEAD > 0) {  // level l+1 of this tile: chunk c - LEAD finished
+                flag = prog + (size_t)(l + 1) * ntiles + q;
+                need = c - WAVE_LEAD;
+            }
+            if (lane == 10 && c == 0 && (int)blockIdx.x == A.stall_item) {
+                flag = A.never;
+                need = 1;
+            }
+            if (flag) {
+                unsigned n = 0;
+                while (*(volatile const int*)flag < need) {
+                    if (*(volatile const int*)A.status != 0) break;
+                    if (++n > A.spin_limit) {
+                        atomicCAS(A.status, 0, 1);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __syncwarp();
+            __threadfence();  // values published before the counters precede this SM's loads
+        }
+        __syncthreads();
+        const int k0 = c * A.zc;
+        const int k1 = min(A.L.nz, k0 + A.zc);
+        if (act) {
+            if (c == 0) col.begin(A.L, src, i0, j, 0, A.L.nz);
+            for (int k = k0; k < k1; ++k) col.plane(A.L, src, dst, A.C, A.c0, A.c1, i0, k);
+        }
+        __syncthreads();  // every thread's stores of the chunk precede thread 0's fence and counter
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            __threadfence();
+            wv_st_release(prog + (size_t)l * ntiles + q, c + 1);
+        }
+    }
+}
+
+template <int KIND, typename TF, typename TC, int BY>
+__global__ void __launch_bounds__(32 * BY, 1) wave_stream_kernel(const __grid_constant__ WaveArgs<TF, TC> A) {
+    const int ntiles = A.ntx * A.nty;
+    const int l = (int)blockIdx.x / ntiles, q = (int)blockIdx.x % ntiles;
+    if (l == A.h - 1) wave_stream<KIND, TF, TC, BY, true>(A, l, q);
+    else wave_stream<KIND, TF, TC, BY, false>(A, l, q);
 }
 
 // ------------------------------------------------------------------- host side
@@ -222,6 +305,58 @@ static cudaError_t wave_pass(const SweepArgs& a, void* const field[2], int p0, c
     return cudaSuccess;
 }
 
+// Stream form of one pass (see wave_stream_kernel): cudaErrorNotReady if the
+// (level, tile) pairs outnumber the CTAs that can be resident at once.
+template <int KIND, typename TF, typename TC, int BY>
+static cudaError_t wave_pass_stream(const SweepArgs& a, void* const field[2], int p0, const WaveShape& sh, int* ws,
+                                    const PersistCtl& ctl, cudaStream_t st, long long* launches) {
+    auto kfn = wave_stream_kernel<KIND, TF, TC, BY>;
+    const int ntiles = sh.ntx * sh.nty;
+    const long long streams = (long long)sh.h * ntiles;
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, 32 * BY, 0))) return e;
+    if (streams > (long long)per * sms) return cudaErrorNotReady;
+    WaveArgs<TF, TC> A{};
+    A.L = a.L;
+    A.f[0] = static_cast<TF*>(field[0]);
+    A.f[1] = static_cast<TF*>(field[1]);
+    for (int m = 0; m < kind_ncoef(a.kind); ++m) A.C.c[m] = static_cast<const TC*>(a.coef[m]);
+    A.c0 = (TF)a.c0;
+    A.c1 = (TF)a.c1;
+    A.p0 = p0;
+    A.h = sh.h;
+    A.lag = sh.lag;
+    A.zc = sh.zc;
+    A.nch = sh.nch;
+    A.ntx = sh.ntx;
+    A.nty = sh.nty;
+    A.nitems = (int)streams;
+    A.status = ws + WAVE_WS_STATUS;
+    A.never = ws + WAVE_WS_NEVER;
+    A.head = ws + WAVE_WS_HEAD;
+    A.flags = ws + WAVE_WS_FLAGS;
+    A.spin_limit = ctl.spin_limit;
+    A.stall_item = ctl.stall_item;
+    if ((e = cudaMemsetAsync(ws + WAVE_WS_NEVER, 0, sizeof(int) * (WAVE_WS_FLAGS - WAVE_WS_NEVER + (size_t)streams),
+                             st)))
+        return e;
+    kfn<<<(unsigned)streams, dim3(32, BY), 0, st>>>(A);
+    if ((e = cudaGetLastError())) return e;
+    if (launches) ++*launches;
+    return cudaSuccess;
+}
+
+template <int KIND, typename TF, typename TC, int BY>
+static cudaError_t wave_pass_any(const SweepArgs& a, void* const field[2], int p0, const WaveShape& sh, int* ws,
+                                 const PersistCtl& ctl, cudaStream_t st, long long* launches) {
+    cudaError_t e = wave_pass_stream<KIND, TF, TC, BY>(a, field, p0, sh, ws, ctl, st, launches);
+    if (e != cudaErrorNotReady) return e;
+    return wave_pass<KIND, TF, TC, BY>(a, field, p0, sh, ws, ctl, st, launches);
+}
+
 template <int KIND, typename TF, typename TC>
 static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
                               size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
@@ -233,9 +368,9 @@ static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, 
         if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
         cudaError_t e = cudaErrorInvalidValue;
         const int p = (p0 + t) & 1;
-        if (tn.by == 4) e = wave_pass<KIND, TF, TC, 4>(a, field, p, sh, w, ctl, st, launches);
-        else if (tn.by == 8) e = wave_pass<KIND, TF, TC, 8>(a, field, p, sh, w, ctl, st, launches);
-        else if (tn.by == 16) e = wave_pass<KIND, TF, TC, 16>(a, field, p, sh, w, ctl, st, launches);
+        if (tn.by == 4) e = wave_pass_any<KIND, TF, TC, 4>(a, field, p, sh, w, ctl, st, launches);
+        else if (tn.by == 8) e = wave_pass_any<KIND, TF, TC, 8>(a, field, p, sh, w, ctl, st, launches);
+        else if (tn.by == 16) e = wave_pass_any<KIND, TF, TC, 16>(a, field, p, sh, w, ctl, st, launches);
         if (e != cudaSuccess) return e;
         t += h;
     }

@@ -130,3 +130,19 @@ def test_wavefront_run_captured_in_a_cuda_graph():
     torch.cuda.synchronize()
     assert s.status() == 0
     assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 10, "plain"))
+
+
+def test_wavefront_unit_form_when_streams_outnumber_resident_ctas():
+    """With more (level, tile) pairs than CTAs that can be resident, each pass runs as units
+    popped in wave order instead of one CTA per (level, tile); both forms must give the
+    plain sweep's result, and a stall in the unit form is reported as a timeout."""
+    from paper_1410_5561_gb300._lib import STATUS
+    p = Problem("7pt_const", 520, 1030, 6, fdt="f32", seed=28, halo=0.5)
+    tn = Tuning(4, 1, 4, 0)  # h = 2, 5 x 258 tiles: 2580 streams
+    assert np.array_equal(_run(p, 5, "plain"), _run(p, 5, "wavefront", tn))
+    s = p.make()
+    s.set_tuning("wavefront", tn)
+    s.set_wait_limit(2000)
+    s.inject_stall(3000)
+    s.run(2)
+    assert STATUS[s.status()] == "STENCIL_ETIMEOUT"

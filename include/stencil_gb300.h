@@ -199,8 +199,8 @@ int stencil_get_field(stencil_t h, void* dst, int where);
  * when ckpt_every <= 0) and the steps in between are recomputed during the
  * backward pass. The coefficient gradients accumulate in FP64. */
 
-/* Workspace bytes both calls below need for (T, ckpt_every): (ceil(T/k) + k + 2)
- * field arrays. */
+/* Workspace bytes both calls below need for (T, ckpt_every): (ceil(T/k) + 2k + 1)
+ * field arrays (the checkpoints, one segment's states and its k + 1 cotangents). */
 size_t stencil_adjoint_workspace_bytes(stencil_t h, int T, int ckpt_every);
 
 /* Like stencil_run(h, T), and stores the checkpoints u_0, u_k, u_2k, ... in
@@ -210,7 +210,11 @@ size_t stencil_adjoint_workspace_bytes(stencil_t h, int T, int ckpt_every);
 int stencil_run_checkpointed(stencil_t h, int T, int ckpt_every, void* workspace, size_t workspace_bytes);
 
 /* Backward pass after stencil_run_checkpointed(h, T, ckpt_every, workspace, ...)
- * with the same coefficients. lambda_T: device, field layout, the cotangent of
+ * with the same coefficients. Per checkpoint segment (k steps): the states are
+ * recomputed from the checkpoint, the k cotangents lambda_t follow by one
+ * transposed step each, and the coefficient gradients of all k steps are then
+ * accumulated in one pass (each FP64 gradient array read and written once per
+ * segment, not once per step; the FP64 fma sequence per element is unchanged). lambda_T: device, field layout, the cotangent of
  * u_T on the interior (its halo is ignored). g_u0: device, field layout; gets
  * dL/du_0 on the interior and 0 elsewhere. g_coef[m], m < n_c: device, gradient
  * layout (STENCIL_GRAD_ARRAY, FP64); overwritten with dL/dC_m on the interior and

@@ -401,7 +401,8 @@ size_t stencil_adjoint_workspace_bytes(stencil_t h, int T, int ckpt_every) {
     if (!h || T < 0) return 0;
     int k = ckpt_k(T, ckpt_every);
     int nck = T > 0 ? (T + k - 1) / k : 1;
-    return (size_t)(nck + k + 2) * h->L.count() * (size_t)dtype_bytes(h->fdt);
+    // checkpoints, the states of one segment, the k + 1 cotangents of one segment
+    return (size_t)(nck + 2 * k + 1) * h->L.count() * (size_t)dtype_bytes(h->fdt);
 }
 
 int stencil_run_checkpointed(stencil_t h, int T, int ckpt_every, void* workspace, size_t workspace_bytes) {
@@ -444,7 +445,9 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
     char* ws = static_cast<char*>(workspace);
     auto ckpt = [&](int c) { return (void*)(ws + (size_t)c * fb); };
     auto state = [&](int j) { return (void*)(ws + (size_t)(nck + j) * fb); };  // j = 1 .. k-1 used
-    void* lam[2] = {ws + (size_t)(nck + k) * fb, ws + (size_t)(nck + k + 1) * fb};
+    // lambda_t lives in slot t mod (k + 1): the k + 1 cotangents of a segment, the segment's
+    // last one shared with the next segment's first
+    auto lam = [&](int t) { return (void*)(ws + (size_t)(nck + k + t % (k + 1)) * fb); };
     SweepArgs a = args_of(h);
     cudaStream_t s = h->stream;
     double* gC[13] = {};
@@ -453,13 +456,15 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
         if (fill_value(gC[m], cnt, DT_F64, 0.0, s) != cudaSuccess) return STENCIL_ECUDA;
         ++h->launches;
     }
-    if (fill_value(lam[1], cnt, h->fdt, 0.0, s) != cudaSuccess) return STENCIL_ECUDA;
-    if (copy_interior_zero_halo(h->L, h->fdt, lambda_T, lam[0], s) != cudaSuccess) return STENCIL_ECUDA;
-    h->launches += 2;
+    for (int i = 0; i <= k; ++i) {  // zero halos: the transpose's "p is interior" condition
+        if (fill_value(ws + (size_t)(nck + k + i) * fb, cnt, h->fdt, 0.0, s) != cudaSuccess) return STENCIL_ECUDA;
+        ++h->launches;
+    }
+    if (copy_interior_zero_halo(h->L, h->fdt, lambda_T, lam(T), s) != cudaSuccess) return STENCIL_ECUDA;
+    ++h->launches;
     // in-segment states inherit the Dirichlet halo of u_0
     for (int j = 1; j < k; ++j)
         if (cudaMemcpyAsync(state(j), ckpt(0), fb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return STENCIL_ECUDA;
-    int cur = 0;
     for (int c = nck - 1; c >= 0 && T > 0; --c) {
         const int t0 = c * k;
         const int t1 = (t0 + k < T) ? t0 + k : T;
@@ -468,14 +473,28 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
             if (plain_step(a, st(j - 1), st(j), s) != cudaSuccess) return STENCIL_ECUDA;
             ++h->launches;
         }
+        // the cotangents of the segment, one transposed step each
         for (int t = t1 - 1; t >= t0; --t) {
-            if (adjoint_step(a, lam[cur], st(t - t0), lam[cur ^ 1], gC, true, s) != cudaSuccess)
-                return STENCIL_ECUDA;
+            if (adjoint_step(a, lam(t + 1), st(t - t0), lam(t), gC, false, s) != cudaSuccess) return STENCIL_ECUDA;
             ++h->launches;
-            cur ^= 1;
         }
+        // then the coefficient gradients of all its steps in one pass (t = t1 - 1 down to t0)
+        const void* lams[64];
+        const void* us[64];
+        int n = 0;
+        for (int t = t1 - 1; t >= t0; --t, ++n) {
+            if (n == 64) {
+                if (adjoint_grads(a, lams, us, n, gC, s) != cudaSuccess) return STENCIL_ECUDA;
+                h->launches += (n + 15) / 16;
+                n = 0;
+            }
+            lams[n] = lam(t + 1);
+            us[n] = st(t - t0);
+        }
+        if (adjoint_grads(a, lams, us, n, gC, s) != cudaSuccess) return STENCIL_ECUDA;
+        h->launches += (n + 15) / 16;
     }
-    if (cudaMemcpyAsync(g_u0, lam[cur], fb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return STENCIL_ECUDA;
+    if (cudaMemcpyAsync(g_u0, lam(0), fb, cudaMemcpyDeviceToDevice, s) != cudaSuccess) return STENCIL_ECUDA;
     return STENCIL_OK;
 }
 

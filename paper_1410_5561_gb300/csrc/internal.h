@@ -54,6 +54,12 @@ cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T,
 cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, const void* u, void* lam_out, double* const* gC,
                          bool accumulate, cudaStream_t s);
 
+// Coefficient gradients of n steps in one pass per group of up to 16 steps:
+// gC[m] += lam[g] * (field value multiplying C_m in the step whose state is u[g]),
+// g = 0 .. n-1 in that order (lam[g] = lambda_{t+1} for the state u[g] = u_t).
+cudaError_t adjoint_grads(const SweepArgs& a, const void* const* lam, const void* const* u, int n, double* const* gC,
+                          cudaStream_t s);
+
 // dst = src on the interior, 0 on every other cell (FP32 / FP64).
 cudaError_t copy_interior_zero_halo(const Layout& L, int dt, const void* src, void* dst, cudaStream_t s);
 

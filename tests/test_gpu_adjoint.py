@@ -194,3 +194,36 @@ def test_single_step_gradient_is_exact_product_fp32():
         want = lam.astype(np.float64) * nb + 0.0  # accumulated onto +0: a -0 product reads +0
         got = s.interior_of(gc[m]).cpu().numpy()
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64)), m
+
+
+@pytest.mark.parametrize("kind,fdt,scheme", [("25pt_var", "f32", "plain"), ("7pt_var", "f32", "blocked"),
+                                             ("25pt_var", "f32", "wavefront")])
+def test_forward_and_backward_captured_in_one_cuda_graph(kind, fdt, scheme):
+    """The differentiable sweep (checkpointed forward, recompute, transposed steps, gradient
+    passes) enqueues only device work, so forward and backward together can be captured in
+    one CUDA graph; each replay reproduces the eager gradients bit for bit."""
+    import torch
+    from paper_1410_5561_gb300.autograd import sweep
+    p, s, u0, coefs, target = _grid_and_inputs(kind, (40, 29, 23), fdt, seed=31)
+    s.set_tuning(scheme, None)
+    T = 9
+    loss_e, gu_e, gc_e = _autograd_grads(s, u0, coefs, target, T)
+    u = u0.clone().requires_grad_(True)
+    c = coefs.clone().requires_grad_(True)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up on the capture stream (workspace, autograd state)
+        s.set_stream(side)
+        (0.5 * ((sweep(u, c, s, T).double() - target.double()) ** 2).sum()).backward()
+    torch.cuda.current_stream().wait_stream(side)
+    u.grad, c.grad = None, None
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        loss = 0.5 * ((sweep(u, c, s, T).double() - target.double()) ** 2).sum()
+        loss.backward()
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert float(loss) == loss_e
+        assert np.array_equal(u.grad.double().cpu().numpy(), gu_e)
+        assert np.array_equal(s.last_coef_grad.cpu().numpy(), gc_e)

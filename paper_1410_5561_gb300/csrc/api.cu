@@ -469,7 +469,24 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
         const int t0 = c * k;
         const int t1 = (t0 + k < T) ? t0 + k : T;
         auto st = [&](int j) { return j == 0 ? ckpt(c) : state(j); };
-        for (int j = 1; j < t1 - t0; ++j) {
+        bool done = false;
+        if (h->scheme == STENCIL_WAVEFRONT && h->ws && t1 - t0 > 1 && t1 - t0 <= 64) {
+            // the segment's states recomputed by one temporally blocked pass whose time levels
+            // each write their own state array (a pass the workspace cannot plan falls back to
+            // one plain step per state; nothing is launched in that case)
+            if (!h->status_armed) {
+                if (cudaMemsetAsync(static_cast<int*>(h->ws) + PERSIST_WS_STATUS, 0, sizeof(int), s) != cudaSuccess)
+                    return STENCIL_ECUDA;
+                h->status_armed = true;
+            }
+            void* lv[64];
+            const int nlev = t1 - t0;  // states t0 .. t1 - 1
+            for (int j = 0; j < nlev; ++j) lv[j] = st(j);
+            cudaError_t e = wave_run_levels(a, lv, nlev, h->wtune, h->ws, GRID_WORKSPACE_BYTES, h->ctl, s, &h->launches);
+            if (e != cudaSuccess && e != cudaErrorInvalidValue) return STENCIL_ECUDA;
+            done = e == cudaSuccess;
+        }
+        for (int j = 1; j < t1 - t0 && !done; ++j) {
             if (plain_step(a, st(j - 1), st(j), s) != cudaSuccess) return STENCIL_ECUDA;
             ++h->launches;
         }

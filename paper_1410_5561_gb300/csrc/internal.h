@@ -97,6 +97,10 @@ struct WaveTune {
 constexpr int WAVE_WS_STATUS = 0, WAVE_WS_NEVER = 1, WAVE_WS_HEAD = 2, WAVE_WS_FLAGS = 3;
 // Workspace bytes one pass of h levels needs (0 if the tuning is malformed for the grid).
 size_t wave_workspace_bytes(const SweepArgs& a, const WaveTune& tn);
+// One pass whose time level l reads levels[l] and writes levels[l + 1] (nlev - 1 levels,
+// at most 64), so that every intermediate state is kept.
+cudaError_t wave_run_levels(const SweepArgs& a, void* const* levels, int nlev, const WaveTune& tn, void* ws,
+                            size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches);
 // T steps in passes of tn.h levels, one launch per pass.
 cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
                      size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches);

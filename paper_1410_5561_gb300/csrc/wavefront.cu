@@ -27,14 +27,14 @@
 namespace stg {
 
 constexpr int WAVE_MAXW = 1024;  // waves per pass
+constexpr int WAVE_MAXLV = 64;   // time levels per pass
 
 template <typename TF, typename TC>
 struct WaveArgs {
     Layout L;
-    TF* f[2];
+    TF* lv[WAVE_MAXLV + 1];  // level l reads lv[l] and writes lv[l + 1]
     CoefPtrs<TC> C;
     TF c0, c1;
-    int p0;         // array holding the pass's input u_t
     int h, lag;     // levels in this pass; chunks between consecutive levels
     int zc, nch;    // planes per chunk; chunks
     int ntx, nty;   // xy tiles
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant_
         const int k0 = c * A.zc;
         const int k1 = min(A.L.nz, k0 + A.zc);
         if (i0 < A.L.nx && j < A.L.ny) {
-            const TF* src = A.f[(A.p0 + l) & 1];
-            TF* dst = A.f[(A.p0 + l + 1) & 1];
+            const TF* src = A.lv[l];
+            TF* dst = A.lv[l + 1];
             if (l == A.h - 1)  // the last level's coefficients are not read again in this pass
                 sweep_column<KIND, TF, TC, PF, true, true>(A.L, src, dst, A.C, A.c0, A.c1, i0, j, k0, k1);
             else
@@ -156,8 +156,8 @@ __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, in
     const int i0 = (qx * 32 + (int)threadIdx.x) * V;
     const int j = qy * BY + (int)threadIdx.y;
     const bool act = i0 < A.L.nx && j < A.L.ny;
-    const TF* src = A.f[(A.p0 + l) & 1];
-    TF* dst = A.f[(A.p0 + l + 1) & 1];
+    const TF* src = A.lv[l];
+    TF* dst = A.lv[l + 1];
     int* prog = A.flags;  // [h][ntiles]: chunks finished
     const bool last = l == A.h - 1;
     Column<KIND, TF, TC, 0, COEF_STREAM, true> col;
@@ -234,7 +234,7 @@ struct WaveShape {
 static bool wave_shape(const SweepArgs& a, int h, int zc, int by, int lag, WaveShape* s) {
     const int R = kind_radius(a.kind);
     const int V = 16 / dtype_bytes(a.fdt);
-    if (h < 1 || zc < R || zc < 1 || by < R || lag < 2) return false;
+    if (h < 1 || h > WAVE_MAXLV || zc < R || zc < 1 || by < R || lag < 2) return false;
     if (by != 4 && by != 8 && by != 16) return false;
     s->h = h;
     s->lag = lag;
@@ -252,18 +252,16 @@ static bool wave_shape(const SweepArgs& a, int h, int zc, int by, int lag, WaveS
 }
 
 template <int KIND, typename TF, typename TC, int BY>
-static cudaError_t wave_pass(const SweepArgs& a, void* const field[2], int p0, const WaveShape& sh, int* ws,
+static cudaError_t wave_pass(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                              const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     constexpr int PF = WaveCfg<KIND, TF, TC>::PF;
     auto kfn = wave_kernel<KIND, TF, TC, BY, PF>;
     WaveArgs<TF, TC> A{};
     A.L = a.L;
-    A.f[0] = static_cast<TF*>(field[0]);
-    A.f[1] = static_cast<TF*>(field[1]);
+    for (int l = 0; l <= sh.h; ++l) A.lv[l] = static_cast<TF*>(lvl[l]);
     for (int m = 0; m < kind_ncoef(a.kind); ++m) A.C.c[m] = static_cast<const TC*>(a.coef[m]);
     A.c0 = (TF)a.c0;
     A.c1 = (TF)a.c1;
-    A.p0 = p0;
     A.h = sh.h;
     A.lag = sh.lag;
     A.zc = sh.zc;
@@ -308,7 +306,7 @@ static cudaError_t wave_pass(const SweepArgs& a, void* const field[2], int p0, c
 // Stream form of one pass (see wave_stream_kernel): cudaErrorNotReady if the
 // (level, tile) pairs outnumber the CTAs that can be resident at once.
 template <int KIND, typename TF, typename TC, int BY>
-static cudaError_t wave_pass_stream(const SweepArgs& a, void* const field[2], int p0, const WaveShape& sh, int* ws,
+static cudaError_t wave_pass_stream(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                                     const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     auto kfn = wave_stream_kernel<KIND, TF, TC, BY>;
     const int ntiles = sh.ntx * sh.nty;
@@ -321,12 +319,10 @@ static cudaError_t wave_pass_stream(const SweepArgs& a, void* const field[2], in
     if (streams > (long long)per * sms) return cudaErrorNotReady;
     WaveArgs<TF, TC> A{};
     A.L = a.L;
-    A.f[0] = static_cast<TF*>(field[0]);
-    A.f[1] = static_cast<TF*>(field[1]);
+    for (int l = 0; l <= sh.h; ++l) A.lv[l] = static_cast<TF*>(lvl[l]);
     for (int m = 0; m < kind_ncoef(a.kind); ++m) A.C.c[m] = static_cast<const TC*>(a.coef[m]);
     A.c0 = (TF)a.c0;
     A.c1 = (TF)a.c1;
-    A.p0 = p0;
     A.h = sh.h;
     A.lag = sh.lag;
     A.zc = sh.zc;
@@ -350,11 +346,11 @@ static cudaError_t wave_pass_stream(const SweepArgs& a, void* const field[2], in
 }
 
 template <int KIND, typename TF, typename TC, int BY>
-static cudaError_t wave_pass_any(const SweepArgs& a, void* const field[2], int p0, const WaveShape& sh, int* ws,
+static cudaError_t wave_pass_any(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                                  const PersistCtl& ctl, cudaStream_t st, long long* launches) {
-    cudaError_t e = wave_pass_stream<KIND, TF, TC, BY>(a, field, p0, sh, ws, ctl, st, launches);
+    cudaError_t e = wave_pass_stream<KIND, TF, TC, BY>(a, lvl, sh, ws, ctl, st, launches);
     if (e != cudaErrorNotReady) return e;
-    return wave_pass<KIND, TF, TC, BY>(a, field, p0, sh, ws, ctl, st, launches);
+    return wave_pass<KIND, TF, TC, BY>(a, lvl, sh, ws, ctl, st, launches);
 }
 
 template <int KIND, typename TF, typename TC>
@@ -367,10 +363,11 @@ static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, 
         if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh)) return cudaErrorInvalidValue;
         if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
         cudaError_t e = cudaErrorInvalidValue;
-        const int p = (p0 + t) & 1;
-        if (tn.by == 4) e = wave_pass_any<KIND, TF, TC, 4>(a, field, p, sh, w, ctl, st, launches);
-        else if (tn.by == 8) e = wave_pass_any<KIND, TF, TC, 8>(a, field, p, sh, w, ctl, st, launches);
-        else if (tn.by == 16) e = wave_pass_any<KIND, TF, TC, 16>(a, field, p, sh, w, ctl, st, launches);
+        void* lvl[WAVE_MAXLV + 1];
+        for (int l = 0; l <= h; ++l) lvl[l] = field[(p0 + t + l) & 1];
+        if (tn.by == 4) e = wave_pass_any<KIND, TF, TC, 4>(a, lvl, sh, w, ctl, st, launches);
+        else if (tn.by == 8) e = wave_pass_any<KIND, TF, TC, 8>(a, lvl, sh, w, ctl, st, launches);
+        else if (tn.by == 16) e = wave_pass_any<KIND, TF, TC, 16>(a, lvl, sh, w, ctl, st, launches);
         if (e != cudaSuccess) return e;
         t += h;
     }
@@ -410,6 +407,49 @@ cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, co
                 return wave_run_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
             break;
     }
+    return cudaErrorInvalidValue;
+}
+
+
+// One pass whose levels read and write the given arrays (levels[l] -> levels[l + 1],
+// l < nlev - 1): every intermediate time level is kept, e.g. the states a checkpointed
+// adjoint recomputes.
+template <int KIND, typename TF, typename TC>
+static cudaError_t wave_levels_t(const SweepArgs& a, void* const* levels, int nlev, const WaveTune& tn, void* ws,
+                                 size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
+    const int h = nlev - 1;
+    WaveShape sh{};
+    if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh)) return cudaErrorInvalidValue;
+    if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
+    int* w = static_cast<int*>(ws);
+    if (tn.by == 4) return wave_pass_any<KIND, TF, TC, 4>(a, levels, sh, w, ctl, st, launches);
+    if (tn.by == 8) return wave_pass_any<KIND, TF, TC, 8>(a, levels, sh, w, ctl, st, launches);
+    if (tn.by == 16) return wave_pass_any<KIND, TF, TC, 16>(a, levels, sh, w, ctl, st, launches);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t wave_run_levels(const SweepArgs& a, void* const* levels, int nlev, const WaveTune& tn, void* ws,
+                            size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches) {
+    if (nlev < 2 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
+    if (!ws) return cudaErrorInvalidValue;
+#define STG_WL(KK, TTF, TTC) return wave_levels_t<KK, TTF, TTC>(a, levels, nlev, tn, ws, ws_bytes, ctl, s, launches)
+    switch (a.kind) {
+        case K7C:
+            if (a.fdt == DT_F32) STG_WL(K7C, float, float);
+            if (a.fdt == DT_F64) STG_WL(K7C, double, double);
+            break;
+        case K7V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K7V, float, float);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K7V, float, __nv_bfloat16);
+            if (a.fdt == DT_F64) STG_WL(K7V, double, double);
+            break;
+        case K25V:
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K25V, float, float);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K25V, float, __nv_bfloat16);
+            if (a.fdt == DT_F64) STG_WL(K25V, double, double);
+            break;
+    }
+#undef STG_WL
     return cudaErrorInvalidValue;
 }
 

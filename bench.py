@@ -446,8 +446,10 @@ def run_ours(args):
     s, u0 = make_grid(H["kind"], n, H["fdt"], H["cdt"], args.seed, device)
     lups = float(n) ** 3 * T
 
-    # autotune the blocked schedule on the real grid, then reset the field
-    tn, table = tuner.best_blocked(s, T, reps=1, max_candidates=6)
+    # autotune the blocked schedule on the real grid (model-guided: the six first candidates
+    # are predicted, at most three timed), then reset the field
+    tn, table = tuner.best_blocked(s, T, reps=1, max_candidates=6, max_timed=3, hbm_gbs=hbm_peak)
+    preds = list(tuner.last_predictions)
     s.set_field(u0, halo=0.0)
 
     # headline: blocked
@@ -580,8 +582,8 @@ def run_ours(args):
         "e2e_sequential": e2e_seq,
         "err_vs_oracle_sampled": err,
         "fma_peaks_tflops": {"f32": fp32_peak / 1e12, "f64": fp64_peak / 1e12},
-        "autotune": [{"tuning": f"dw={t.dw} nf={t.nf} warps={t.warps} xtile={t.xtile}", "s": sec}
-                     for t, sec in table],
+        "autotune": [{"tuning": f"dw={t.dw} nf={t.nf} warps={t.warps} xtile={t.xtile}",
+                      "predicted_s": p, "measured_s": m} for t, p, m in preds],
     }
     del s, u0
     torch.cuda.empty_cache()
@@ -672,12 +674,14 @@ def sampled_oracle_error(s, kind, n, fdt, cdt, T, seed):
 
 
 def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
-    """Plain vs tuned blocked sweep for every stencil and precision: GLUP/s, the model bytes
-    per LUP, the roofline (the slower of the HBM bound at the model bytes and the FP-pipe
-    bound) and the achieved fraction of it, and each result's error against the FP64 oracle
-    on sampled points."""
+    """Plain vs tuned blocked sweep (diamonds in shared memory, model-guided tuner) vs the
+    wavefront schedule through L2, for every stencil and precision: GLUP/s, the model bytes per
+    LUP, the roofline (the slower of the HBM bound at the model bytes and the FP-pipe bound)
+    and the achieved fraction of it, and each result's error against the FP64 oracle on
+    sampled points."""
     import torch
     from paper_1410_5561_gb300 import model, tuner
+    from paper_1410_5561_gb300.stencil import Tuning
     rows = []
     for kind, n, fdt, cdt, T in PER_STENCIL:
         s, u0 = make_grid(kind, n, fdt, cdt, seed, device)
@@ -691,7 +695,7 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
         s.run(T)
         err_plain = sampled_oracle_error(s, kind, n, fdt, cdt, T, seed)
         try:
-            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+            tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=6, max_timed=3, hbm_gbs=hbm_peak)
             tb = timed(s, T, 2, 1) / 2
             tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
             bb = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)
@@ -700,6 +704,22 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
             err_blk = sampled_oracle_error(s, kind, n, fdt, cdt, T, seed)
         except RuntimeError:
             tb, tun, bb, err_blk = None, None, None, None
+        # wavefront through L2: the better of two tunings (2 and 4 levels per pass)
+        R = 4 if kind == "25pt_var" else 1
+        tw, tun_w, err_w = None, None, None
+        for wt in (Tuning(4 * R, max(R, 4), 8, 0), Tuning(8 * R, max(R, 4), 4, 0)):
+            try:
+                s.set_tuning("wavefront", wt)
+            except RuntimeError:
+                continue
+            t_ = timed(s, T, 2, 1) / 2
+            if tw is None or t_ < tw:
+                tw, tun_w = t_, wt
+        if tun_w is not None:
+            s.set_tuning("wavefront", tun_w)
+            s.set_field(u0, halo=0.0)
+            s.run(T)
+            err_w = sampled_oracle_error(s, kind, n, fdt, cdt, T, seed)
         roof_p = min(hbm_peak / bp, alu_glups)
         roof_b = min(hbm_peak / bb, alu_glups) if bb else None
         gp = lups / tp / 1e9
@@ -710,13 +730,17 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
             "blocked_glups": gb,
             "blocked_over_plain": gb / gp if gb else None,
             "blocked_tuning": tun,
+            "wavefront_glups": lups / tw / 1e9 if tw else None,
+            "wavefront_tuning": {"dw": tun_w.dw, "zchunk": tun_w.nf, "rows": tun_w.warps} if tun_w else None,
+            "autotune": [{"tuning": f"dw={t.dw} nf={t.nf} warps={t.warps} xtile={t.xtile}", "predicted_s": p_,
+                          "measured_s": m_} for t, p_, m_ in tuner.last_predictions] if tun else None,
             "model_bytes_per_lup": {"plain": bp, "blocked": bb},
             "roofline_glups": {"hbm_plain": hbm_peak / bp, "hbm_blocked": hbm_peak / bb if bb else None,
                                "alu": alu_glups},
             "roofline_frac": {"plain": gp / roof_p, "blocked": gb / roof_b if gb else None,
                               "plain_bound": "hbm" if hbm_peak / bp <= alu_glups else "alu",
                               "blocked_bound": ("hbm" if hbm_peak / bb <= alu_glups else "alu") if bb else None},
-            "err_vs_oracle": {"plain": err_plain, "blocked": err_blk},
+            "err_vs_oracle": {"plain": err_plain, "blocked": err_blk, "wavefront": err_w},
         })
         del s, u0
         torch.cuda.empty_cache()
@@ -794,7 +818,7 @@ def energy_table(device, seed, min_seconds: float = 2.0):
                 bpl = model.bytes_per_lup(kind, fdt, cdt, "plain")
                 tun = None
             else:
-                tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=4)
+                tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=6, max_timed=3)
                 bpl = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)
                 tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
             s.run(T)

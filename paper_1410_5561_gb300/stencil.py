@@ -26,7 +26,7 @@ def kind_id(kind) -> int:
     return KINDS[kind] if isinstance(kind, str) else int(kind)
 
 
-@dataclass
+@dataclass(frozen=True)
 class Tuning:
     """Blocked-schedule tunables: diamond width D_w, frontlines N_F, warps per CTA
     (the thread group sharing one extruded diamond), x columns per CTA."""

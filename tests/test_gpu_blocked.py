@@ -231,3 +231,24 @@ def test_persistent_run_captured_in_a_cuda_graph(kind, fdt, cdt, tn):
     torch.cuda.synchronize()
     assert s.status() == 0
     assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 14, "plain"))
+
+
+def test_model_guided_tuner_times_three_and_keeps_the_best():
+    """The tuner predicts the first six candidates (Eq. 5 bytes at the kernel's streaming rate,
+    useful columns, frontlines, register pressure), times at most three of them, and its
+    choice is within 10 % of the best of all six timed exhaustively."""
+    import torch
+    from paper_1410_5561_gb300 import tuner
+    p = Problem("7pt_const", 320, 320, 320, fdt="f32", seed=3)
+    s = p.make()
+    T = 24
+    tn, table = tuner.best_blocked(s, T, reps=2, max_candidates=6, max_timed=3)
+    assert 1 <= len(table) <= 3
+    preds = tuner.last_predictions
+    assert len(preds) >= len(table) and all(pr > 0 for _, pr, _ in preds)
+    full, full_table = tuner.best_blocked(s, T, reps=2, max_candidates=6)
+    best_full = min(t for _, t in full_table)
+    s.set_tuning("blocked", tn)
+    torch.cuda.synchronize()
+    mine = tuner._time_run(s, T, 3)
+    assert mine <= 1.10 * best_full, (tn, mine, full, best_full)

@@ -80,3 +80,57 @@ def test_tight_uneven_tiles_are_candidates(optin):
             assert tuner.x_tiles(n, Tuning(8, 2, 16, want), 1, 4) == (5 if n == 512 else 9)
         finally:
             g.close()
+
+
+def test_predictions_follow_the_model_terms(optin):
+    """predict: register spills, one frontline instead of two, fewer useful columns and a
+    larger code balance (Eq. 5) each make a tuning slower; FP64 plain sweeps are ALU-bound
+    once the FP64 rate is given."""
+    g = HostGrid(C.STENCIL_7PT_CONST, 1024, 1024, 1024)
+    try:
+        p = lambda t: tuner.predict(g, 100, "blocked", t)  # noqa: E731
+        assert p(Tuning(8, 2, 16, 112)) < p(Tuning(8, 1, 16, 112))        # frontlines
+        assert p(Tuning(8, 2, 16, 112)) < p(Tuning(8, 2, 16, 128))        # 2 items per warp spill
+        assert p(Tuning(8, 2, 16, 112)) < p(Tuning(6, 2, 16, 116))        # Eq. 5: 4 vs 5.33 B/LUP
+        assert p(Tuning(8, 2, 16, 112)) < p(Tuning(8, 2, 16, 104))        # 9 tiles vs 10 per row
+        best = min(tuner.candidates(g)[:6], key=p)
+        assert (best.dw, best.nf, best.warps, best.xtile) == (8, 2, 16, 112)
+    finally:
+        g.close()
+    d = HostGrid(C.STENCIL_7PT_CONST, 512, 512, 512, dtype=torch.float64)
+    try:
+        mem = tuner.predict(d, 100, "plain", None)
+        alu = tuner.predict(d, 100, "plain", None, fp_peak=1.26e12)
+        assert alu > 3 * mem  # 7 FP64 instructions per LUP at 1.26 TFLOP/s outlast 16 B at HBM speed
+    finally:
+        d.close()
+
+
+def test_autotune_times_at_most_three_and_prunes(optin, monkeypatch):
+    """autotune times the best predictions only: at most max_timed candidates, none predicted
+    more than 1.5x slower than the best, and it returns the fastest measured one; the table
+    lists every candidate with its prediction (scaled by the first measurement)."""
+    g = HostGrid(C.STENCIL_7PT_CONST, 512, 512, 512)
+    timed = []
+    g.set_tuning = lambda scheme, t=None: timed.append((scheme, t))
+    truth = {}
+
+    def fake_time(s, T, reps):
+        sc, t = timed[-1]
+        # pretend the device runs 10 % slower than predicted, plus noise that favours the
+        # second-best prediction
+        v = tuner.predict(g, T, sc, t) * 1.1
+        truth[(sc, t)] = v * (0.8 if len(truth) == 1 else 1.0)
+        return truth[(sc, t)]
+
+    monkeypatch.setattr(tuner, "_time_run", fake_time)
+    try:
+        sc, tn, table = tuner.autotune(g, 100, use_cache=False, max_timed=3, max_candidates=6)
+        measured = [(lab, p, m) for lab, p, m in table if m is not None]
+        assert 1 <= len(measured) <= 3
+        p0 = min(p for _, p, _ in table)
+        assert all(p <= tuner.PRUNE * p0 * 1.0000001 for _, p, _ in measured)
+        assert len(table) == 7  # plain and six blocked tunings, each with a prediction
+        assert min(truth, key=truth.get) == (sc, tn)
+    finally:
+        g.close()

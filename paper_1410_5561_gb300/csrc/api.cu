@@ -292,12 +292,14 @@ int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning) {
     }
     if (scheme == STENCIL_WAVEFRONT) {
         const int R = kind_radius(h->kind);
-        WaveTune w{2, R > 8 ? R : 8, 8, 2};  // default: two levels per pass, 8-plane chunks, 8-row tiles
+        WaveTune w{2, R > 8 ? R : 8, 8, 2, 0};  // default: two levels per pass, 8-plane chunks, 8-row tiles
         if (tuning) {
             if (tuning->dw < 2 * R || tuning->dw % (2 * R) != 0) return STENCIL_EINVAL;
+            if (tuning->xtile != 0 && tuning->xtile != 2) return STENCIL_EINVAL;
             w.h = tuning->dw / (2 * R);
             w.zc = tuning->nf;
             w.by = tuning->warps;
+            w.cp = tuning->xtile;
         }
         const size_t need = wave_workspace_bytes(args_of(h), w);
         if (need == 0) return STENCIL_EINVAL;

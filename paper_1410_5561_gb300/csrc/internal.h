@@ -90,6 +90,7 @@ constexpr size_t GRID_WORKSPACE_BYTES = size_t(16) << 20;
 // l-1 by `lag` chunks.
 struct WaveTune {
     int h, zc, by, lag;
+    int cp;  // planes of coefficients each thread copies ahead into shared memory (0 or 2)
 };
 // Workspace words (ints) of the wavefront schedule: the status word (shared with the
 // persistent blocked schedule), a flag no unit sets, the unit counter, then one

@@ -21,6 +21,8 @@
 // again from L2 by the next level a few chunks later (written-back
 // intermediates add s_f per level). The L2 holds about (LAG + 1) ZC planes of
 // every array while a pass runs.
+#include <type_traits>
+
 #include "internal.h"
 #include "sweep_column.cuh"
 
@@ -148,9 +150,10 @@ constexpr int WAVE_LEAD = 3;
 
 // All chunks of one (level, tile) stream; COEF_STREAM for the last level, whose
 // coefficient loads are evict-first (no later level of the pass reads them).
-template <int KIND, typename TF, typename TC, int BY, bool COEF_STREAM>
+template <int KIND, typename TF, typename TC, int BY, bool COEF_STREAM, int CP>
 __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, int q) {
     constexpr int V = 16 / sizeof(TF);
+    extern __shared__ __align__(16) unsigned char wave_smem[];
     const int ntiles = A.ntx * A.nty;
     const int qx = q % A.ntx, qy = q / A.ntx;
     const int i0 = (qx * 32 + (int)threadIdx.x) * V;
@@ -160,7 +163,18 @@ __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, in
     TF* dst = A.lv[l + 1];
     int* prog = A.flags;  // [h][ntiles]: chunks finished
     const bool last = l == A.h - 1;
-    Column<KIND, TF, TC, 0, COEF_STREAM, true> col;
+    // CP = 0: loads issued per plane; CP > 0: every load of a plane copied CP planes ahead into this
+    // thread's shared-memory slots (field vectors first, then the coefficient vectors)
+    using Col = std::conditional_t<(CP > 0), ColumnAsync<KIND, TF, TC, COEF_STREAM, (CP > 0 ? CP : 1)>,
+                                   Column<KIND, TF, TC, 0, COEF_STREAM, true, 0>>;
+    Col col;
+    constexpr int NT = 32 * BY;
+    constexpr int CB = (int)sizeof(Vec<TC, V>);
+    constexpr int SF = ColumnAsync<KIND, TF, TC, COEF_STREAM, 1>::SF;
+    const int tid = (int)(threadIdx.y * 32 + threadIdx.x);
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(wave_smem);
+    const uint32_t fslot = s0 + (uint32_t)(tid * 16), fstep = (uint32_t)(NT * 16);
+    const uint32_t cslot = s0 + (uint32_t)((CP > 0 ? CP : 1) * SF * NT * 16 + tid * CB), cstep = (uint32_t)(NT * CB);
     for (int c = 0; c < A.nch; ++c) {
         if (threadIdx.y == 0) {
             const int lane = threadIdx.x;
@@ -199,7 +213,10 @@ __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, in
         const int k0 = c * A.zc;
         const int k1 = min(A.L.nz, k0 + A.zc);
         if (act) {
-            if (c == 0) col.begin(A.L, src, i0, j, 0, A.L.nz);
+            if (c == 0) {
+                if constexpr (CP > 0) col.begin(A.L, src, A.C, i0, j, 0, A.L.nz, fslot, fstep, cslot, cstep);
+                else col.begin(A.L, src, i0, j, 0, A.L.nz);
+            }
             for (int k = k0; k < k1; ++k) col.plane(A.L, src, dst, A.C, A.c0, A.c1, i0, k);
         }
         __syncthreads();  // every thread's stores of the chunk precede thread 0's fence and counter
@@ -210,12 +227,12 @@ __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, in
     }
 }
 
-template <int KIND, typename TF, typename TC, int BY>
+template <int KIND, typename TF, typename TC, int BY, int CP>
 __global__ void __launch_bounds__(32 * BY, 1) wave_stream_kernel(const __grid_constant__ WaveArgs<TF, TC> A) {
     const int ntiles = A.ntx * A.nty;
     const int l = (int)blockIdx.x / ntiles, q = (int)blockIdx.x % ntiles;
-    if (l == A.h - 1) wave_stream<KIND, TF, TC, BY, true>(A, l, q);
-    else wave_stream<KIND, TF, TC, BY, false>(A, l, q);
+    if (l == A.h - 1) wave_stream<KIND, TF, TC, BY, true, CP>(A, l, q);
+    else wave_stream<KIND, TF, TC, BY, false, CP>(A, l, q);
 }
 
 // ------------------------------------------------------------------- host side
@@ -227,17 +244,18 @@ template <> struct WaveCfg<K25V, float, float> { static constexpr int PF = 0; };
 // Geometry of one pass: chunks, tiles, waves and units; false if the tuning is
 // malformed for this grid.
 struct WaveShape {
-    int h, lag, zc, nch, ntx, nty, nwaves, nitems;
+    int h, lag, zc, nch, ntx, nty, nwaves, nitems, cp;
     size_t flag_words;
 };
 
-static bool wave_shape(const SweepArgs& a, int h, int zc, int by, int lag, WaveShape* s) {
+static bool wave_shape(const SweepArgs& a, int h, int zc, int by, int lag, WaveShape* s, int cp = 0) {
     const int R = kind_radius(a.kind);
     const int V = 16 / dtype_bytes(a.fdt);
     if (h < 1 || h > WAVE_MAXLV || zc < R || zc < 1 || by < R || lag < 2) return false;
     if (by != 4 && by != 8 && by != 16) return false;
     s->h = h;
     s->lag = lag;
+    s->cp = cp;
     s->zc = zc;
     s->nch = (a.L.nz + zc - 1) / zc;
     s->ntx = (a.L.nx + 32 * V - 1) / (32 * V);
@@ -305,17 +323,27 @@ static cudaError_t wave_pass(const SweepArgs& a, void* const* lvl, const WaveSha
 
 // Stream form of one pass (see wave_stream_kernel): cudaErrorNotReady if the
 // (level, tile) pairs outnumber the CTAs that can be resident at once.
-template <int KIND, typename TF, typename TC, int BY>
+template <int KIND, typename TF, typename TC, int BY, int CP>
 static cudaError_t wave_pass_stream(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                                     const PersistCtl& ctl, cudaStream_t st, long long* launches) {
-    auto kfn = wave_stream_kernel<KIND, TF, TC, BY>;
+    auto kfn = wave_stream_kernel<KIND, TF, TC, BY, CP>;
+    constexpr int V = 16 / sizeof(TF);
+    constexpr int SF = ColumnAsync<KIND, TF, TC, false, 1>::SF;
+    const size_t smem = (size_t)CP * 32 * BY * (SF * 16 + KindTraits<KIND>::NC * sizeof(Vec<TC, V>));
+    if constexpr (CP > 0) {
+        int dev0 = 0, optin = 0;
+        cudaGetDevice(&dev0);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev0);
+        if (smem > (size_t)optin || sh.zc < KindTraits<KIND>::R + CP) return cudaErrorNotReady;
+    }
     const int ntiles = sh.ntx * sh.nty;
     const long long streams = (long long)sh.h * ntiles;
     int dev = 0, sms = 0, per = 0;
     cudaError_t e;
+    if ((e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem))) return e;
     if ((e = cudaGetDevice(&dev))) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, 32 * BY, 0))) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, 32 * BY, smem))) return e;
     if (streams > (long long)per * sms) return cudaErrorNotReady;
     WaveArgs<TF, TC> A{};
     A.L = a.L;
@@ -339,7 +367,7 @@ static cudaError_t wave_pass_stream(const SweepArgs& a, void* const* lvl, const 
     if ((e = cudaMemsetAsync(ws + WAVE_WS_NEVER, 0, sizeof(int) * (WAVE_WS_FLAGS - WAVE_WS_NEVER + (size_t)streams),
                              st)))
         return e;
-    kfn<<<(unsigned)streams, dim3(32, BY), 0, st>>>(A);
+    kfn<<<(unsigned)streams, dim3(32, BY), smem, st>>>(A);
     if ((e = cudaGetLastError())) return e;
     if (launches) ++*launches;
     return cudaSuccess;
@@ -348,7 +376,9 @@ static cudaError_t wave_pass_stream(const SweepArgs& a, void* const* lvl, const 
 template <int KIND, typename TF, typename TC, int BY>
 static cudaError_t wave_pass_any(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                                  const PersistCtl& ctl, cudaStream_t st, long long* launches) {
-    cudaError_t e = wave_pass_stream<KIND, TF, TC, BY>(a, lvl, sh, ws, ctl, st, launches);
+    cudaError_t e = cudaErrorNotReady;
+    if (sh.cp == 2) e = wave_pass_stream<KIND, TF, TC, BY, 2>(a, lvl, sh, ws, ctl, st, launches);
+    if (e == cudaErrorNotReady) e = wave_pass_stream<KIND, TF, TC, BY, 0>(a, lvl, sh, ws, ctl, st, launches);
     if (e != cudaErrorNotReady) return e;
     return wave_pass<KIND, TF, TC, BY>(a, lvl, sh, ws, ctl, st, launches);
 }
@@ -360,7 +390,7 @@ static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, 
     for (int t = 0; t < T;) {
         const int h = T - t < tn.h ? T - t : tn.h;
         WaveShape sh{};
-        if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh)) return cudaErrorInvalidValue;
+        if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh, tn.cp)) return cudaErrorInvalidValue;
         if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
         cudaError_t e = cudaErrorInvalidValue;
         void* lvl[WAVE_MAXLV + 1];
@@ -419,7 +449,7 @@ static cudaError_t wave_levels_t(const SweepArgs& a, void* const* levels, int nl
                                  size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     const int h = nlev - 1;
     WaveShape sh{};
-    if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh)) return cudaErrorInvalidValue;
+    if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh, tn.cp)) return cudaErrorInvalidValue;
     if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
     int* w = static_cast<int*>(ws);
     if (tn.by == 4) return wave_pass_any<KIND, TF, TC, 4>(a, levels, sh, w, ctl, st, launches);

@@ -25,9 +25,10 @@ def _run(p, T, scheme, tuning=None):
     return s.get_field().cpu().numpy()
 
 
-# Tuning(D_w = 2R h, z-chunk planes, rows per tile, ignored)
-R1_WAVE = [Tuning(4, 1, 4, 0), Tuning(6, 3, 8, 0), Tuning(8, 2, 16, 0), Tuning(2, 5, 4, 0)]
-R4_WAVE = [Tuning(16, 4, 4, 0), Tuning(24, 5, 8, 0), Tuning(8, 8, 16, 0), Tuning(32, 4, 8, 0)]
+# Tuning(D_w = 2R h, z-chunk planes, rows per tile, coefficient planes prefetched into shared memory)
+R1_WAVE = [Tuning(4, 1, 4, 0), Tuning(6, 3, 8, 2), Tuning(8, 2, 16, 0), Tuning(2, 5, 4, 2)]
+R4_WAVE = [Tuning(16, 4, 4, 0), Tuning(24, 5, 8, 2), Tuning(8, 8, 16, 0), Tuning(32, 4, 8, 0),
+           Tuning(16, 4, 16, 2)]
 
 
 @pytest.mark.parametrize("tn", R1_WAVE, ids=lambda t: f"dw{t.dw}zc{t.nf}by{t.warps}")
@@ -87,7 +88,8 @@ def test_wavefront_rejects_malformed_tunings():
     for tn in [Tuning(12, 4, 8, 0),   # D_w not a multiple of 2R
                Tuning(16, 3, 8, 0),   # chunk thinner than R
                Tuning(16, 4, 2, 0),   # tile rows fewer than R
-               Tuning(16, 4, 12, 0)]:  # rows per tile not 4, 8 or 16
+               Tuning(16, 4, 12, 0),   # rows per tile not 4, 8 or 16
+               Tuning(16, 4, 8, 3)]:   # coefficient prefetch other than 0 or 2 planes
         with pytest.raises(StencilError):
             s.set_tuning("wavefront", tn)
     w = Problem("7pt_const", 20, 20, 20, fdt="f32", seed=1).make(workspace=False)

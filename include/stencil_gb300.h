@@ -142,15 +142,20 @@ int stencil_set_coeffs(stencil_t h, const double* scalars, const void* const* ar
  * the interior of field_a, which becomes the current array (time 0). */
 int stencil_set_field(stencil_t h, const void* src, double halo_value, int where);
 
-/* Select the schedule used by run(): STENCIL_PLAIN (one launch per step),
+/* Select the schedule used by run(): STENCIL_PLAIN (one launch per step;
+ * tuning->nf = 2 makes every thread copy the loads of its next two planes
+ * into shared memory ahead of use, 0 loads each plane when it is updated,
+ * NULL: 2 for the 25-point stencil with BF16 coefficients, where it measured
+ * faster, else 0; other tuning fields ignored),
  * STENCIL_WAVEFRONT (wavefront temporal blocking through L2: Section II-A's
  * thread group sharing one cache block, here every CTA of the GPU sharing the
  * L2; each launch advances h = dw / (2R) steps: time level l of the pass
  * sweeps z chunks of nf planes (nf >= R) two chunks behind level l-1, on xy
  * tiles of 32 vectors by `warps` rows (4, 8 or 16, >= R), the CTAs waiting on
- * bounded completion flags; xtile is ignored; NULL: h = 2, 8-plane chunks, 8
- * rows; needs a bound workspace, else STENCIL_EINVAL; bit-identical to the
- * plain sweep), or
+ * bounded completion flags; xtile = 2 copies every load two planes ahead into
+ * shared memory where nf >= R + 2 and it fits, 0 does not; NULL: h = 2,
+ * 8-plane chunks, 8 rows, no copies ahead; needs a bound workspace, else
+ * STENCIL_EINVAL; bit-identical to the plain sweep), or
  * STENCIL_BLOCKED with *tuning (NULL: library default: D_w = 8R, N_F = 2 where it
  * fits, 16 warps for R = 1, the widest x tile whose rows fit one warp of vectors), or
  * STENCIL_AUTO (plain for FP64 fields and the 25-point stencil, where the plain sweep

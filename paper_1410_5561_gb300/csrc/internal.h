@@ -26,6 +26,7 @@ struct SweepArgs {
     const void* coef[13];  // padded coefficient arrays (device)
     double c0, c1;         // Listing 1 scalars (7-point constant)
     double halo;           // Dirichlet value of every halo cell
+    int plain_prefetch;    // plain sweep: planes each thread copies ahead into shared memory (0 or 2)
 };
 
 // Blocked-sweep tunables (D_w, N_F, warps per CTA, x-tile width).

@@ -42,10 +42,33 @@ plain_sweep_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst, C
     sweep_column<KIND, TF, TC, PF, true>(L, src, dst, C, c0, c1, i0, j, k0, k1);
 }
 
+// The plain sweep with every load of a plane copied D planes ahead into per-thread shared-memory
+// slots (ColumnAsync): the copies in flight hold shared memory, not registers.
+template <int KIND, typename TF, typename TC, int BY, int D>
+__global__ void __launch_bounds__(32 * BY) plain_async_kernel(Layout L, const TF* __restrict__ src, TF* __restrict__ dst,
+                                                              CoefPtrs<TC> C, TF c0, TF c1, int zchunk) {
+    constexpr int V = 16 / sizeof(TF);
+    using Col = ColumnAsync<KIND, TF, TC, true, D>;
+    extern __shared__ __align__(16) unsigned char plain_smem[];
+    const int i0 = (blockIdx.x * 32 + threadIdx.x) * V;
+    const int j = blockIdx.y * BY + threadIdx.y;
+    if (i0 >= L.nx || j >= L.ny) return;
+    const int k0 = blockIdx.z * zchunk;
+    const int k1 = min(L.nz, k0 + zchunk);
+    if (k0 >= k1) return;
+    constexpr int NT = 32 * BY;
+    const int tid = (int)(threadIdx.y * 32 + threadIdx.x);
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(plain_smem);
+    Col col;
+    col.begin(L, src, C, i0, j, k0, k1, s0 + (uint32_t)(tid * 16), (uint32_t)(NT * 16),
+              s0 + (uint32_t)(D * Col::SF * NT * 16 + tid * Col::CB), (uint32_t)(NT * Col::CB));
+    for (int k = k0; k < k1; ++k) col.plane(L, src, dst, C, c0, c1, i0, k);
+}
+
 // Resident CTAs per SM of one kernel instantiation times the SM count, per device
 // (one cache per instantiation: the template arguments name the kernel).
 template <int KIND, typename TF, typename TC, typename KernelT>
-static int plain_slots(KernelT kernel, int threads) {
+static int plain_slots(KernelT kernel, int threads, size_t smem = 0) {
     static std::mutex mu;
     static int cached[64] = {0};
     int dev = 0;
@@ -54,7 +77,7 @@ static int plain_slots(KernelT kernel, int threads) {
     if (cached[dev] == 0) {
         int sms = 0, per = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, 0) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem) != cudaSuccess) return 0;
         cached[dev] = sms * (per > 0 ? per : 1);
     }
     return cached[dev];
@@ -89,10 +112,24 @@ static cudaError_t launch_plain(const SweepArgs& a, const void* src, void* dst, 
     if (L.nx == 0 || L.ny == 0 || L.nz == 0) return cudaSuccess;
     CoefPtrs<TC> C{};
     for (int m = 0; m < KindTraits<KIND>::NC; ++m) C.c[m] = static_cast<const TC*>(a.coef[m]);
-    auto kernel = plain_sweep_kernel<KIND, TF, TC, BY, PF>;
     dim3 block(32, BY);
     unsigned gx = (unsigned)((L.nx + 32 * V - 1) / (32 * V));
     unsigned gy = (unsigned)((L.ny + BY - 1) / BY);
+    if (a.plain_prefetch == 2) {
+        constexpr int D = 2;
+        using Col = ColumnAsync<KIND, TF, TC, true, D>;
+        auto kernel = plain_async_kernel<KIND, TF, TC, BY, D>;
+        const size_t smem = (size_t)D * 32 * BY * (Col::SF * 16 + KindTraits<KIND>::NC * Col::CB);
+        cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int nchunks = plain_chunks((long long)gx * gy, L.nz, KindTraits<KIND>::R,
+                                         plain_slots<KIND, TF, TC>(kernel, 32 * BY, smem));
+        const int zchunk = (L.nz + nchunks - 1) / nchunks;
+        kernel<<<dim3(gx, gy, (unsigned)nchunks), block, smem, s>>>(L, static_cast<const TF*>(src), static_cast<TF*>(dst),
+                                                                     C, (TF)a.c0, (TF)a.c1, zchunk);
+        return cudaGetLastError();
+    }
+    auto kernel = plain_sweep_kernel<KIND, TF, TC, BY, PF>;
     const int nchunks = plain_chunks((long long)gx * gy, L.nz, KindTraits<KIND>::R, plain_slots<KIND, TF, TC>(kernel, 32 * BY));
     const int zchunk = (L.nz + nchunks - 1) / nchunks;
     dim3 grid(gx, gy, (unsigned)nchunks);

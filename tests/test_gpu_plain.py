@@ -111,3 +111,24 @@ def test_set_and_get_field_through_every_memory_kind(shape, fdt):
             s.get_field(out)
             torch.cuda.synchronize()
             assert torch.equal(out.cpu(), ref), (name, oname)
+
+
+@pytest.mark.parametrize("kind,shape,fdt,cdt", [
+    ("7pt_const", (150, 37, 29), "f32", None), ("7pt_const", (70, 21, 18), "f64", None),
+    ("7pt_var", (133, 29, 19), "f32", None), ("7pt_var", (40, 43, 17), "f32", "bf16"),
+    ("7pt_var", (33, 19, 14), "f64", None), ("25pt_var", (141, 35, 27), "f32", None),
+    ("25pt_var", (27, 33, 19), "f32", "bf16"), ("25pt_var", (38, 25, 30), "f64", None),
+])
+@pytest.mark.parametrize("T", [1, 4])
+def test_prefetched_plain_sweep_is_bitwise_equal(kind, shape, fdt, cdt, T):
+    """The plain sweep with every load of a plane copied two planes ahead into shared memory
+    (plain tuning nf = 2) runs the same update on the same operands: bit-identical results."""
+    from paper_1410_5561_gb300.stencil import Tuning
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=41, halo=0.375)
+    a = p.make()
+    a.set_tuning("plain")
+    a.run(T)
+    b = p.make()
+    b.set_tuning("plain", Tuning(0, 2, 0, 0))
+    b.run(T)
+    assert np.array_equal(a.get_field().cpu().numpy(), b.get_field().cpu().numpy())

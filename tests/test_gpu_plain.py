@@ -126,7 +126,7 @@ def test_prefetched_plain_sweep_is_bitwise_equal(kind, shape, fdt, cdt, T):
     from paper_1410_5561_gb300.stencil import Tuning
     p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=41, halo=0.375)
     a = p.make()
-    a.set_tuning("plain")
+    a.set_tuning("plain", Tuning(0, 0, 0, 0))
     a.run(T)
     b = p.make()
     b.set_tuning("plain", Tuning(0, 2, 0, 0))

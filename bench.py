@@ -704,10 +704,12 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
             err_blk = sampled_oracle_error(s, kind, n, fdt, cdt, T, seed)
         except RuntimeError:
             tb, tun, bb, err_blk = None, None, None, None
-        # wavefront through L2: the better of two tunings (2 and 4 levels per pass)
+        # wavefront through L2: the better of two tunings measured best on GB300 (25-point: 2 levels
+        # with 16-plane chunks and loads copied ahead, or 3 levels; 7-point: 2 or 6 levels)
         R = 4 if kind == "25pt_var" else 1
         tw, tun_w, err_w = None, None, None
-        for wt in (Tuning(4 * R, max(R, 4), 8, 0), Tuning(8 * R, max(R, 4), 4, 0)):
+        wcands = (Tuning(16, 16, 8, 2), Tuning(24, 8, 4, 0)) if R == 4 else (Tuning(4, 4, 16, 0), Tuning(12, 8, 4, 0))
+        for wt in wcands:
             try:
                 s.set_tuning("wavefront", wt)
             except RuntimeError:
@@ -731,7 +733,8 @@ def per_stencil(device, seed, hbm_peak, fp32_peak, fp64_peak):
             "blocked_over_plain": gb / gp if gb else None,
             "blocked_tuning": tun,
             "wavefront_glups": lups / tw / 1e9 if tw else None,
-            "wavefront_tuning": {"dw": tun_w.dw, "zchunk": tun_w.nf, "rows": tun_w.warps} if tun_w else None,
+            "wavefront_tuning": {"dw": tun_w.dw, "zchunk": tun_w.nf, "rows": tun_w.warps,
+                                 "prefetch": tun_w.xtile} if tun_w else None,
             "autotune": [{"tuning": f"dw={t.dw} nf={t.nf} warps={t.warps} xtile={t.xtile}", "predicted_s": p_,
                           "measured_s": m_} for t, p_, m_ in tuner.last_predictions] if tun else None,
             "model_bytes_per_lup": {"plain": bp, "blocked": bb},

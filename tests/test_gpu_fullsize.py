@@ -10,8 +10,8 @@ recipe itself; the device grid is drawn by the torch version of the same recipe,
 the test checks that the two agree bit for bit at the crop before comparing outputs.
 
 Each case runs the plain sweep, the blocked schedule with every tuning the benchmark's
-autotuner may pick (the first candidates in its order) and STENCIL_AUTO, all on the
-same inputs; each result is checked against the oracle within the element-wise bound
+autotuner may pick (the first candidates in its order), the wavefront schedule with the
+tunings the benchmark times, and STENCIL_AUTO, all on the same inputs; each result is checked against the oracle within the element-wise bound
 of ``Problem.elementwise_tol`` (the weights of a row sum to at most 1, so each step
 adds at most 2 x (roundings per update) x eps x max|u|).
 """
@@ -21,7 +21,7 @@ import torch
 
 import oracle
 from paper_1410_5561_gb300 import inputs, tuner
-from paper_1410_5561_gb300.stencil import RADIUS, Stencil
+from paper_1410_5561_gb300.stencil import RADIUS, Stencil, Tuning
 from tests._util import EPS, ROUNDINGS
 
 pytestmark = pytest.mark.gpu
@@ -120,7 +120,12 @@ def test_full_size_sampled_parity(kind, n, fdt, cdt, T, ncand):
 
     scale = max(float(np.max(np.abs(c[2]))) for c in crops)
     tol = max(T, 1) * 2 * ROUNDINGS[kind] * EPS[fdt] * scale
-    runs = [("plain", None)] + [("blocked", t) for t in tunings] + [("auto", None)]
+    # the wavefront tunings the benchmark times (2 and 6 levels for R = 1; 2 levels with copies
+    # ahead and 3 levels for R = 4)
+    waves = [Tuning(16, 16, 8, 2), Tuning(24, 8, 4, 0)] if kind == "25pt_var" else \
+        [Tuning(4, 4, 16, 0), Tuning(12, 8, 4, 0)]
+    runs = [("plain", None)] + [("blocked", t) for t in tunings] + [("wavefront", t) for t in waves] + \
+        [("auto", None)]
     for scheme, tn in runs:
         s.set_field(u0, halo=0.0)
         s.set_tuning(scheme, tn)

@@ -791,19 +791,26 @@ def dw_sweep(device, seed, per_dw: int = 2):
 ENERGY_CASES = [
     ("7pt_const", 1024, "f32", None, 100),
     ("7pt_const", 512, "f32", None, 100),
+    ("7pt_const", 512, "f64", None, 100),
     ("7pt_var", 384, "f32", None, 50),
     ("7pt_var", 384, "f32", "bf16", 50),
 ]
+# the wavefront tuning measured best per stencil and precision on GB300 (D_w, chunk planes, rows,
+# copies ahead): six levels with 8-plane chunks and 4-row tiles, or two levels with 4-plane
+# chunks and 16-row tiles for the 7-point variable FP32 sweep
+ENERGY_WAVE = {("7pt_const", "f32"): (12, 8, 4, 0), ("7pt_const", "f64"): (12, 8, 4, 0),
+               ("7pt_var", "f32"): (4, 4, 16, 0), ("7pt_var", "bf16"): (12, 8, 4, 0)}
 
 
 def energy_table(device, seed, min_seconds: float = 2.0):
-    """Board energy per LUP, plain vs blocked (the paper's Section IV question on the GPU):
-    NVML's total-energy counter read around at least ``min_seconds`` of back-to-back runs of
-    each schedule; the idle board power, read first over one second with nothing of ours
+    """Board energy per LUP, plain vs blocked vs wavefront (the paper's Section IV question on the
+    GPU): NVML's total-energy counter read around at least ``min_seconds`` of back-to-back runs
+    of each schedule; the idle board power, read first over one second with nothing of ours
     running, gives the dynamic share. Blocked runs use the tuning the benchmark's autotuner
     chose for the grid (cached), else the tuner's first candidate."""
     import torch
     from paper_1410_5561_gb300 import energy, model, tuner
+    from paper_1410_5561_gb300.stencil import Tuning
     meter = energy.EnergyMeter(energy.device_uuid(device))
     if not meter.available:
         return {"unavailable": meter.reason}
@@ -815,15 +822,22 @@ def energy_table(device, seed, min_seconds: float = 2.0):
         s, _ = make_grid(kind, n, fdt, cdt, seed, device)
         lups = float(n) ** 3 * T
         row = {"stencil": kind, "grid": n, "field": fdt, "coef": cdt or fdt, "T": T}
-        for scheme in ("plain", "blocked"):
+        for scheme in ("plain", "blocked", "wavefront"):
             if scheme == "plain":
                 s.set_tuning("plain")
                 bpl = model.bytes_per_lup(kind, fdt, cdt, "plain")
                 tun = None
-            else:
+            elif scheme == "blocked":
                 tn, _ = tuner.best_blocked(s, T, reps=1, max_candidates=6, max_timed=3)
                 bpl = model.bytes_per_lup(kind, fdt, cdt, "blocked", tn.dw)
                 tun = {"dw": tn.dw, "nf": tn.nf, "warps": tn.warps, "xtile": tn.xtile}
+            else:
+                wt = Tuning(*ENERGY_WAVE[(kind, cdt or fdt)])
+                s.set_tuning("wavefront", wt)
+                h = wt.dw // 2  # R = 1
+                sf = 8 if fdt == "f64" else 4
+                bpl = (model.bytes_per_lup(kind, fdt, cdt, "plain") + (h - 1) * sf) / h
+                tun = {"dw": wt.dw, "zchunk": wt.nf, "rows": wt.warps}
             s.run(T)
             r = energy.measure(meter, lambda: s.run(T), lups, min_seconds=min_seconds, sync=sync)
             if r is None:
@@ -835,6 +849,8 @@ def energy_table(device, seed, min_seconds: float = 2.0):
                            "tuning": tun}
         if row.get("plain") and row.get("blocked"):
             row["blocked_over_plain_energy"] = row["blocked"]["pj_per_lup"] / row["plain"]["pj_per_lup"]
+        if row.get("plain") and row.get("wavefront"):
+            row["wavefront_over_plain_energy"] = row["wavefront"]["pj_per_lup"] / row["plain"]["pj_per_lup"]
         rows.append(row)
         del s
         torch.cuda.empty_cache()

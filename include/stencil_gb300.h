@@ -218,8 +218,10 @@ int stencil_run_checkpointed(stencil_t h, int T, int ckpt_every, void* workspace
  * with the same coefficients. Per checkpoint segment (k steps): the states are
  * recomputed from the checkpoint (with STENCIL_WAVEFRONT tuned: by one
  * temporally blocked pass whose time levels each write their own state array;
- * otherwise one plain step per state), the k cotangents lambda_t follow by one
- * transposed step each, and the coefficient gradients of all k steps are then
+ * otherwise one plain step per state), the k cotangents lambda_t follow (with
+ * STENCIL_WAVEFRONT tuned: by one temporally blocked pass of transposed steps,
+ * each level writing its own cotangent array; otherwise one transposed step
+ * each), and the coefficient gradients of all k steps are then
  * accumulated in one pass (each FP64 gradient array read and written once per
  * segment, not once per step; the FP64 fma sequence per element is unchanged). lambda_T: device, field layout, the cotangent of
  * u_T on the interior (its halo is ignored). g_u0: device, field layout; gets

@@ -11,200 +11,28 @@
 //   dL/du_0 = lambda_0.
 // Zero halos in lambda and in the coefficient arrays make the "p is interior"
 // condition of the transpose automatic. Coefficient gradients accumulate in FP64.
+#include "adjoint_column.cuh"
 #include "internal.h"
 
 namespace stg {
 
-template <typename TC>
-struct AdjCoef {
-    const TC* c[13];
-};
 struct AdjGrad {
     double* g[13];
 };
 
-// One adjoint step over the interior: lam_out = A^T lam_in (interior), gC += lam_in * u
-// terms. A warp covers 32 x vectors of V = 16/sizeof(field) points (128-bit loads),
-// warps are stacked along y, and each thread walks a chunk of z planes. The transpose
-// sums C0 lam first, then for d = 1..R and axis x, y, z the minus neighbour's term and
-// the plus neighbour's term.
-template <int KIND, typename TF, typename TC>
-struct AdjSides {
-    // coefficient arrays weighing the minus and plus neighbour of axis a at distance d
-    static __device__ __forceinline__ int minus(int d, int a) {
-        return KIND == K7V ? 1 + 2 * a : 3 * (d - 1) + a + 1;
-    }
-    static __device__ __forceinline__ int plus(int d, int a) { return KIND == K7V ? 2 + 2 * a : 3 * (d - 1) + a + 1; }
-};
-
+// One transposed step over the interior: lam_out = A^T lam_in (lambda_column). A warp covers
+// 32 x vectors of V = 16/sizeof(field) points (128-bit loads), warps are stacked along y, and
+// each thread walks a chunk of z planes.
 template <int KIND, typename TF, typename TC, int BY>
 __global__ void __launch_bounds__(32 * BY) adjoint_vec_kernel(Layout L, const TF* __restrict__ lam_in,
-                                                              const TF* __restrict__ u, TF* __restrict__ lam_out,
-                                                              AdjCoef<TC> C, AdjGrad G, int accumulate, int zchunk) {
-    constexpr int R = KindTraits<KIND>::R;
+                                                              TF* __restrict__ lam_out, CoefPtrs<TC> C, int zchunk) {
     constexpr int V = 16 / sizeof(TF);
-    constexpr int J = (R + V - 1) / V;  // neighbour vectors on each side along x
-    constexpr int XL = (2 * J + 1) * V;
-    using A = Ar<TF>;
-    using SD = AdjSides<KIND, TF, TC>;
     const int i0 = (blockIdx.x * 32 + threadIdx.x) * V;
     const int j = blockIdx.y * BY + threadIdx.y;
     if (i0 >= L.nx || j >= L.ny) return;
     const int k0 = blockIdx.z * zchunk;
     const int k1 = min(L.nz, k0 + zchunk);
-    const size_t sy = (size_t)L.px, sz = L.plane();
-    const bool full = i0 + V <= L.nx;
-    for (int k = k0; k < k1; ++k) {
-        const size_t p = L.at(i0, j, k);
-        TF lx[XL], ux[XL];  // x lines around the vector: [i0 - J V, i0 + (J + 1) V)
-#pragma unroll
-        for (int q = -J; q <= J; ++q) {
-            const Vec<TF, V> wl = ldv_ro<TF, V>(lam_in + p + (ptrdiff_t)q * V);
-            const Vec<TF, V> wu = ldv_ro<TF, V>(u + p + (ptrdiff_t)q * V);
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                lx[(q + J) * V + e] = wl.v[e];
-                ux[(q + J) * V + e] = wu.v[e];
-            }
-        }
-        TF r[V];
-        {
-            const Vec<TC, V> c0 = ldv_ro<TC, V>(C.c[0] + p);
-#pragma unroll
-            for (int e = 0; e < V; ++e) r[e] = A::mul(Cvt<TF, TC>::f(c0.v[e]), lx[J * V + e]);
-        }
-#pragma unroll
-        for (int d = 1; d <= R; ++d) {
-            // x: coefficient lines of the two arrays at this distance
-            {
-                const TC* cm = C.c[SD::minus(d, 0)];
-                const TC* cpl = C.c[SD::plus(d, 0)];
-                TF cxm[XL], cxp[XL];
-#pragma unroll
-                for (int q = -J; q <= J; ++q) {
-                    const Vec<TC, V> a = ldv_ro<TC, V>(cm + p + (ptrdiff_t)q * V);
-                    const Vec<TC, V> b = ldv_ro<TC, V>(cpl + p + (ptrdiff_t)q * V);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        cxm[(q + J) * V + e] = Cvt<TF, TC>::f(a.v[e]);
-                        cxp[(q + J) * V + e] = Cvt<TF, TC>::f(b.v[e]);
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    const int xc = J * V + e;
-                    r[e] = A::fma(cxm[xc - d], lx[xc - d], r[e]);
-                    r[e] = A::fma(cxp[xc + d], lx[xc + d], r[e]);
-                }
-            }
-            // y and z
-#pragma unroll
-            for (int a = 1; a < 3; ++a) {
-                const size_t o = (size_t)d * (a == 1 ? sy : sz);
-                const Vec<TC, V> cmv = ldv_ro<TC, V>(C.c[SD::minus(d, a)] + p - o);
-                const Vec<TF, V> lmv = ldv_ro<TF, V>(lam_in + p - o);
-                const Vec<TC, V> cpv = ldv_ro<TC, V>(C.c[SD::plus(d, a)] + p + o);
-                const Vec<TF, V> lpv = ldv_ro<TF, V>(lam_in + p + o);
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    r[e] = A::fma(Cvt<TF, TC>::f(cmv.v[e]), lmv.v[e], r[e]);
-                    r[e] = A::fma(Cvt<TF, TC>::f(cpv.v[e]), lpv.v[e], r[e]);
-                }
-            }
-        }
-        if (full) {
-            Vec<TF, V> o;
-#pragma unroll
-            for (int e = 0; e < V; ++e) o.v[e] = r[e];
-            stv<TF, V>(lam_out + p, o);
-        } else {
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                if (i0 + e < L.nx) lam_out[p + e] = r[e];
-        }
-        if (!accumulate) continue;
-        // coefficient gradients (FP64): term m of point p multiplies lam(p) by the field
-        // value(s) it weighs at step t. The arrays are updated in groups whose loads all
-        // precede their stores (the arrays may alias as far as the compiler knows, so a
-        // store would otherwise hold back every later load).
-        double ld[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) ld[e] = (double)lx[J * V + e];
-        // weights of array m: 7-point C0 u(p), C(2a+1) u(p + e_a), C(2a+2) u(p - e_a);
-        // 25-point C00 u(p), C(3(d-1)+a+1) (u(p + d e_a) + u(p - d e_a))
-        auto weights = [&](int m, double* w) {
-            if (m == 0) {
-#pragma unroll
-                for (int e = 0; e < V; ++e) w[e] = (double)ux[J * V + e];
-                return;
-            }
-            const int d = KIND == K7V ? 1 : (m - 1) / 3 + 1;
-            const int a = KIND == K7V ? (m - 1) / 2 : (m - 1) % 3;
-            const int side = KIND == K7V ? ((m - 1) % 2 == 0 ? 1 : -1) : 0;  // 0: both
-            TF up[V], um[V];
-            if (a == 0) {
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    up[e] = ux[J * V + e + (d <= J * V ? d : 0)];
-                    um[e] = ux[J * V + e - (d <= J * V ? d : 0)];
-                }
-            } else {
-                const size_t o = (size_t)d * (a == 1 ? sy : sz);
-                const Vec<TF, V> vp = ldv_ro<TF, V>(u + p + o);
-                const Vec<TF, V> vm = ldv_ro<TF, V>(u + p - o);
-#pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    up[e] = vp.v[e];
-                    um[e] = vm.v[e];
-                }
-            }
-            // the 25-point pair sum is formed in the field precision, as the forward step
-            // forms it, so the gradient is that of the computed operator
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                w[e] = (double)(side > 0 ? up[e] : side < 0 ? um[e] : A::add(up[e], um[e]));
-        };
-        constexpr int NC = KindTraits<KIND>::NC;
-        constexpr int GRP = 4;
-#pragma unroll
-        for (int m0 = 0; m0 < NC; m0 += GRP) {
-            double gv[GRP][V], w[GRP][V];
-#pragma unroll
-            for (int gi = 0; gi < GRP; ++gi) {
-                const int m = m0 + gi;
-                if (m >= NC) continue;
-                weights(m, w[gi]);
-                const double* gp = G.g[m] + p;
-                if (full) {
-#pragma unroll
-                    for (int h = 0; h < V; h += 2) {
-                        const double2 g = *reinterpret_cast<const double2*>(gp + h);
-                        gv[gi][h] = g.x;
-                        gv[gi][h + 1] = g.y;
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) gv[gi][e] = i0 + e < L.nx ? gp[e] : 0.0;
-                }
-            }
-#pragma unroll
-            for (int gi = 0; gi < GRP; ++gi) {
-                const int m = m0 + gi;
-                if (m >= NC) continue;
-                double* gp = G.g[m] + p;
-#pragma unroll
-                for (int e = 0; e < V; ++e) gv[gi][e] = __fma_rn(ld[e], w[gi][e], gv[gi][e]);
-                if (full) {
-#pragma unroll
-                    for (int h = 0; h < V; h += 2) *reinterpret_cast<double2*>(gp + h) = make_double2(gv[gi][h], gv[gi][h + 1]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        if (i0 + e < L.nx) gp[e] = gv[gi][e];
-                }
-            }
-        }
-    }
+    lambda_column<KIND, TF, TC, false>(L, lam_in, lam_out, C, i0, j, k0, k1);
 }
 
 // Coefficient gradients of several steps in one pass: for the steps t = t_hi, t_hi - 1,
@@ -379,41 +207,31 @@ __global__ void copy_interior_zero_halo_kernel(Layout L, const TF* __restrict__ 
 }
 
 template <int KIND, typename TF, typename TC>
-static cudaError_t adj_step(const SweepArgs& a, const void* lam_in, const void* u, void* lam_out,
-                            double* const* gC, bool accumulate, cudaStream_t s) {
+static cudaError_t adj_step(const SweepArgs& a, const void* lam_in, void* lam_out, cudaStream_t s) {
     const Layout& L = a.L;
-    AdjCoef<TC> C{};
-    AdjGrad G{};
-    for (int m = 0; m < KindTraits<KIND>::NC; ++m) {
-        C.c[m] = static_cast<const TC*>(a.coef[m]);
-        G.g[m] = gC[m];
-    }
+    CoefPtrs<TC> C{};
+    for (int m = 0; m < KindTraits<KIND>::NC; ++m) C.c[m] = static_cast<const TC*>(a.coef[m]);
     constexpr int BY = 4;
     constexpr int V = 16 / sizeof(TF);
     const int zchunk = 16;
     dim3 block(32, BY, 1);
     dim3 grid((unsigned)((L.nx + 32 * V - 1) / (32 * V)), (unsigned)((L.ny + BY - 1) / BY),
               (unsigned)((L.nz + zchunk - 1) / zchunk));
-    adjoint_vec_kernel<KIND, TF, TC, BY><<<grid, block, 0, s>>>(
-        L, static_cast<const TF*>(lam_in), static_cast<const TF*>(u), static_cast<TF*>(lam_out), C, G,
-        accumulate ? 1 : 0, zchunk);
+    adjoint_vec_kernel<KIND, TF, TC, BY><<<grid, block, 0, s>>>(L, static_cast<const TF*>(lam_in),
+                                                                static_cast<TF*>(lam_out), C, zchunk);
     return cudaGetLastError();
 }
 
-cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, const void* u, void* lam_out, double* const* gC,
-                         bool accumulate, cudaStream_t s) {
+cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, void* lam_out, cudaStream_t s) {
     if (a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
     if (a.kind == K7V) {
-        if (a.fdt == DT_F32 && a.cdt == DT_F32) return adj_step<K7V, float, float>(a, lam_in, u, lam_out, gC, accumulate, s);
-        if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-            return adj_step<K7V, float, __nv_bfloat16>(a, lam_in, u, lam_out, gC, accumulate, s);
-        if (a.fdt == DT_F64) return adj_step<K7V, double, double>(a, lam_in, u, lam_out, gC, accumulate, s);
+        if (a.fdt == DT_F32 && a.cdt == DT_F32) return adj_step<K7V, float, float>(a, lam_in, lam_out, s);
+        if (a.fdt == DT_F32 && a.cdt == DT_BF16) return adj_step<K7V, float, __nv_bfloat16>(a, lam_in, lam_out, s);
+        if (a.fdt == DT_F64) return adj_step<K7V, double, double>(a, lam_in, lam_out, s);
     } else if (a.kind == K25V) {
-        if (a.fdt == DT_F32 && a.cdt == DT_F32)
-            return adj_step<K25V, float, float>(a, lam_in, u, lam_out, gC, accumulate, s);
-        if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-            return adj_step<K25V, float, __nv_bfloat16>(a, lam_in, u, lam_out, gC, accumulate, s);
-        if (a.fdt == DT_F64) return adj_step<K25V, double, double>(a, lam_in, u, lam_out, gC, accumulate, s);
+        if (a.fdt == DT_F32 && a.cdt == DT_F32) return adj_step<K25V, float, float>(a, lam_in, lam_out, s);
+        if (a.fdt == DT_F32 && a.cdt == DT_BF16) return adj_step<K25V, float, __nv_bfloat16>(a, lam_in, lam_out, s);
+        if (a.fdt == DT_F64) return adj_step<K25V, double, double>(a, lam_in, lam_out, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -499,9 +499,20 @@ int stencil_run_adjoint(stencil_t h, int T, int ckpt_every, const void* lambda_T
             if (plain_step(a, st(j - 1), st(j), s) != cudaSuccess) return STENCIL_ECUDA;
             ++h->launches;
         }
-        // the cotangents of the segment, one transposed step each
-        for (int t = t1 - 1; t >= t0; --t) {
-            if (adjoint_step(a, lam(t + 1), st(t - t0), lam(t), gC, false, s) != cudaSuccess) return STENCIL_ECUDA;
+        // the cotangents of the segment: with the wavefront schedule tuned, one temporally blocked
+        // pass of transposed steps whose levels each write their own cotangent array; otherwise
+        // one transposed step per launch
+        bool lam_done = false;
+        if (h->scheme == STENCIL_WAVEFRONT && h->ws && t1 - t0 <= 64) {
+            void* lv[65];
+            for (int i = 0; i <= t1 - t0; ++i) lv[i] = lam(t1 - i);
+            cudaError_t e = wave_run_levels(a, lv, t1 - t0 + 1, h->wtune, h->ws, GRID_WORKSPACE_BYTES, h->ctl, s,
+                                            &h->launches, true);
+            if (e != cudaSuccess && e != cudaErrorInvalidValue) return STENCIL_ECUDA;
+            lam_done = e == cudaSuccess;
+        }
+        for (int t = t1 - 1; t >= t0 && !lam_done; --t) {
+            if (adjoint_step(a, lam(t + 1), lam(t), s) != cudaSuccess) return STENCIL_ECUDA;
             ++h->launches;
         }
         // then the coefficient gradients of all its steps in one pass (t = t1 - 1 down to t0)

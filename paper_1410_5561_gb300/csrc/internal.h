@@ -50,10 +50,8 @@ cudaError_t copy_rows(const Layout& L, int eb, const void* src, void* dst, bool 
 cudaError_t blocked_run(const SweepArgs& a, void* const field[2], int p0, int T,
                         const BlockedTune& tune, cudaStream_t s, long long* launches);
 
-// One adjoint step: lam_out = A^T lam_in over the interior; if accumulate,
-// gC[m] += lam_in * (field value multiplying C_m) in FP64.
-cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, const void* u, void* lam_out, double* const* gC,
-                         bool accumulate, cudaStream_t s);
+// One transposed step of the adjoint's cotangent recursion: lam_out = A^T lam_in over the interior.
+cudaError_t adjoint_step(const SweepArgs& a, const void* lam_in, void* lam_out, cudaStream_t s);
 
 // Coefficient gradients of n steps in one pass per group of up to 16 steps:
 // gC[m] += lam[g] * (field value multiplying C_m in the step whose state is u[g]),
@@ -100,9 +98,11 @@ constexpr int WAVE_WS_STATUS = 0, WAVE_WS_NEVER = 1, WAVE_WS_HEAD = 2, WAVE_WS_F
 // Workspace bytes one pass of h levels needs (0 if the tuning is malformed for the grid).
 size_t wave_workspace_bytes(const SweepArgs& a, const WaveTune& tn);
 // One pass whose time level l reads levels[l] and writes levels[l + 1] (nlev - 1 levels,
-// at most 64), so that every intermediate state is kept.
+// at most 64), so that every intermediate state is kept. With transposed, each level is the
+// adjoint's transposed step (levels[l + 1] = A^T levels[l]; variable-coefficient stencils).
 cudaError_t wave_run_levels(const SweepArgs& a, void* const* levels, int nlev, const WaveTune& tn, void* ws,
-                            size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches);
+                            size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches,
+                            bool transposed = false);
 // T steps in passes of tn.h levels, one launch per pass.
 cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
                      size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches);

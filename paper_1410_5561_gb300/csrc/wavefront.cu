@@ -23,6 +23,7 @@
 // every array while a pass runs.
 #include <type_traits>
 
+#include "adjoint_column.cuh"
 #include "internal.h"
 #include "sweep_column.cuh"
 
@@ -63,7 +64,8 @@ __host__ __device__ inline void wave_levels(int w, int h, int lag, int nch, int&
     lmin = d <= 0 ? 0 : (d + lag - 1) / lag;
 }
 
-template <int KIND, typename TF, typename TC, int BY, int PF>
+// OP = 0: the forward step (sweep_column); OP = 1: the adjoint's transposed step (lambda_column).
+template <int KIND, typename TF, typename TC, int BY, int PF, int OP>
 __global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant__ WaveArgs<TF, TC> A) {
     constexpr int V = 16 / sizeof(TF);
     __shared__ int s_item[2];
@@ -123,7 +125,9 @@ __global__ void __launch_bounds__(32 * BY, 1) wave_kernel(const __grid_constant_
         if (i0 < A.L.nx && j < A.L.ny) {
             const TF* src = A.lv[l];
             TF* dst = A.lv[l + 1];
-            if (l == A.h - 1)  // the last level's coefficients are not read again in this pass
+            if constexpr (OP == 1)
+                lambda_column<KIND, TF, TC, true>(A.L, src, dst, A.C, i0, j, k0, k1);
+            else if (l == A.h - 1)  // the last level's coefficients are not read again in this pass
                 sweep_column<KIND, TF, TC, PF, true, true>(A.L, src, dst, A.C, A.c0, A.c1, i0, j, k0, k1);
             else
                 sweep_column<KIND, TF, TC, PF, false, true>(A.L, src, dst, A.C, A.c0, A.c1, i0, j, k0, k1);
@@ -150,7 +154,7 @@ constexpr int WAVE_LEAD = 3;
 
 // All chunks of one (level, tile) stream; COEF_STREAM for the last level, whose
 // coefficient loads are evict-first (no later level of the pass reads them).
-template <int KIND, typename TF, typename TC, int BY, bool COEF_STREAM, int CP>
+template <int KIND, typename TF, typename TC, int BY, bool COEF_STREAM, int CP, int OP>
 __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, int q) {
     constexpr int V = 16 / sizeof(TF);
     extern __shared__ __align__(16) unsigned char wave_smem[];
@@ -213,11 +217,15 @@ __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, in
         const int k0 = c * A.zc;
         const int k1 = min(A.L.nz, k0 + A.zc);
         if (act) {
-            if (c == 0) {
-                if constexpr (CP > 0) col.begin(A.L, src, A.C, i0, j, 0, A.L.nz, fslot, fstep, cslot, cstep);
-                else col.begin(A.L, src, i0, j, 0, A.L.nz);
+            if constexpr (OP == 1) {
+                lambda_column<KIND, TF, TC, true>(A.L, src, dst, A.C, i0, j, k0, k1);
+            } else {
+                if (c == 0) {
+                    if constexpr (CP > 0) col.begin(A.L, src, A.C, i0, j, 0, A.L.nz, fslot, fstep, cslot, cstep);
+                    else col.begin(A.L, src, i0, j, 0, A.L.nz);
+                }
+                for (int k = k0; k < k1; ++k) col.plane(A.L, src, dst, A.C, A.c0, A.c1, i0, k);
             }
-            for (int k = k0; k < k1; ++k) col.plane(A.L, src, dst, A.C, A.c0, A.c1, i0, k);
         }
         __syncthreads();  // every thread's stores of the chunk precede thread 0's fence and counter
         if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -227,12 +235,12 @@ __device__ __forceinline__ void wave_stream(const WaveArgs<TF, TC>& A, int l, in
     }
 }
 
-template <int KIND, typename TF, typename TC, int BY, int CP>
+template <int KIND, typename TF, typename TC, int BY, int CP, int OP>
 __global__ void __launch_bounds__(32 * BY, 1) wave_stream_kernel(const __grid_constant__ WaveArgs<TF, TC> A) {
     const int ntiles = A.ntx * A.nty;
     const int l = (int)blockIdx.x / ntiles, q = (int)blockIdx.x % ntiles;
-    if (l == A.h - 1) wave_stream<KIND, TF, TC, BY, true, CP>(A, l, q);
-    else wave_stream<KIND, TF, TC, BY, false, CP>(A, l, q);
+    if (l == A.h - 1) wave_stream<KIND, TF, TC, BY, true, CP, OP>(A, l, q);
+    else wave_stream<KIND, TF, TC, BY, false, CP, OP>(A, l, q);
 }
 
 // ------------------------------------------------------------------- host side
@@ -269,11 +277,11 @@ static bool wave_shape(const SweepArgs& a, int h, int zc, int by, int lag, WaveS
     return true;
 }
 
-template <int KIND, typename TF, typename TC, int BY>
+template <int KIND, typename TF, typename TC, int BY, int OP>
 static cudaError_t wave_pass(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                              const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     constexpr int PF = WaveCfg<KIND, TF, TC>::PF;
-    auto kfn = wave_kernel<KIND, TF, TC, BY, PF>;
+    auto kfn = wave_kernel<KIND, TF, TC, BY, PF, OP>;
     WaveArgs<TF, TC> A{};
     A.L = a.L;
     for (int l = 0; l <= sh.h; ++l) A.lv[l] = static_cast<TF*>(lvl[l]);
@@ -323,10 +331,10 @@ static cudaError_t wave_pass(const SweepArgs& a, void* const* lvl, const WaveSha
 
 // Stream form of one pass (see wave_stream_kernel): cudaErrorNotReady if the
 // (level, tile) pairs outnumber the CTAs that can be resident at once.
-template <int KIND, typename TF, typename TC, int BY, int CP>
+template <int KIND, typename TF, typename TC, int BY, int CP, int OP>
 static cudaError_t wave_pass_stream(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                                     const PersistCtl& ctl, cudaStream_t st, long long* launches) {
-    auto kfn = wave_stream_kernel<KIND, TF, TC, BY, CP>;
+    auto kfn = wave_stream_kernel<KIND, TF, TC, BY, CP, OP>;
     constexpr int V = 16 / sizeof(TF);
     constexpr int SF = ColumnAsync<KIND, TF, TC, false, 1>::SF;
     const size_t smem = (size_t)CP * 32 * BY * (SF * 16 + KindTraits<KIND>::NC * sizeof(Vec<TC, V>));
@@ -373,14 +381,14 @@ static cudaError_t wave_pass_stream(const SweepArgs& a, void* const* lvl, const 
     return cudaSuccess;
 }
 
-template <int KIND, typename TF, typename TC, int BY>
+template <int KIND, typename TF, typename TC, int BY, int OP = 0>
 static cudaError_t wave_pass_any(const SweepArgs& a, void* const* lvl, const WaveShape& sh, int* ws,
                                  const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     cudaError_t e = cudaErrorNotReady;
-    if (sh.cp == 2) e = wave_pass_stream<KIND, TF, TC, BY, 2>(a, lvl, sh, ws, ctl, st, launches);
-    if (e == cudaErrorNotReady) e = wave_pass_stream<KIND, TF, TC, BY, 0>(a, lvl, sh, ws, ctl, st, launches);
+    if (OP == 0 && sh.cp == 2) e = wave_pass_stream<KIND, TF, TC, BY, (OP == 0 ? 2 : 0), OP>(a, lvl, sh, ws, ctl, st, launches);
+    if (e == cudaErrorNotReady) e = wave_pass_stream<KIND, TF, TC, BY, 0, OP>(a, lvl, sh, ws, ctl, st, launches);
     if (e != cudaErrorNotReady) return e;
-    return wave_pass<KIND, TF, TC, BY>(a, lvl, sh, ws, ctl, st, launches);
+    return wave_pass<KIND, TF, TC, BY, OP>(a, lvl, sh, ws, ctl, st, launches);
 }
 
 template <int KIND, typename TF, typename TC>
@@ -444,7 +452,7 @@ cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, co
 // One pass whose levels read and write the given arrays (levels[l] -> levels[l + 1],
 // l < nlev - 1): every intermediate time level is kept, e.g. the states a checkpointed
 // adjoint recomputes.
-template <int KIND, typename TF, typename TC>
+template <int KIND, typename TF, typename TC, int OP>
 static cudaError_t wave_levels_t(const SweepArgs& a, void* const* levels, int nlev, const WaveTune& tn, void* ws,
                                  size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
     const int h = nlev - 1;
@@ -452,31 +460,43 @@ static cudaError_t wave_levels_t(const SweepArgs& a, void* const* levels, int nl
     if (!wave_shape(a, h, tn.zc, tn.by, tn.lag, &sh, tn.cp)) return cudaErrorInvalidValue;
     if (sizeof(int) * (WAVE_WS_FLAGS + sh.flag_words) > ws_bytes) return cudaErrorInvalidValue;
     int* w = static_cast<int*>(ws);
-    if (tn.by == 4) return wave_pass_any<KIND, TF, TC, 4>(a, levels, sh, w, ctl, st, launches);
-    if (tn.by == 8) return wave_pass_any<KIND, TF, TC, 8>(a, levels, sh, w, ctl, st, launches);
-    if (tn.by == 16) return wave_pass_any<KIND, TF, TC, 16>(a, levels, sh, w, ctl, st, launches);
+    if (tn.by == 4) return wave_pass_any<KIND, TF, TC, 4, OP>(a, levels, sh, w, ctl, st, launches);
+    if (tn.by == 8) return wave_pass_any<KIND, TF, TC, 8, OP>(a, levels, sh, w, ctl, st, launches);
+    if (tn.by == 16) return wave_pass_any<KIND, TF, TC, 16, OP>(a, levels, sh, w, ctl, st, launches);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t wave_run_levels(const SweepArgs& a, void* const* levels, int nlev, const WaveTune& tn, void* ws,
-                            size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches) {
+                            size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches, bool transposed) {
     if (nlev < 2 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
     if (!ws) return cudaErrorInvalidValue;
-#define STG_WL(KK, TTF, TTC) return wave_levels_t<KK, TTF, TTC>(a, levels, nlev, tn, ws, ws_bytes, ctl, s, launches)
+#define STG_WL(KK, TTF, TTC, OP) return wave_levels_t<KK, TTF, TTC, OP>(a, levels, nlev, tn, ws, ws_bytes, ctl, s, launches)
+    if (transposed) {  // the adjoint's cotangent recursion (variable-coefficient stencils)
+        if (a.kind == K7V) {
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K7V, float, float, 1);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K7V, float, __nv_bfloat16, 1);
+            if (a.fdt == DT_F64) STG_WL(K7V, double, double, 1);
+        } else if (a.kind == K25V) {
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K25V, float, float, 1);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K25V, float, __nv_bfloat16, 1);
+            if (a.fdt == DT_F64) STG_WL(K25V, double, double, 1);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (a.kind) {
         case K7C:
-            if (a.fdt == DT_F32) STG_WL(K7C, float, float);
-            if (a.fdt == DT_F64) STG_WL(K7C, double, double);
+            if (a.fdt == DT_F32) STG_WL(K7C, float, float, 0);
+            if (a.fdt == DT_F64) STG_WL(K7C, double, double, 0);
             break;
         case K7V:
-            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K7V, float, float);
-            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K7V, float, __nv_bfloat16);
-            if (a.fdt == DT_F64) STG_WL(K7V, double, double);
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K7V, float, float, 0);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K7V, float, __nv_bfloat16, 0);
+            if (a.fdt == DT_F64) STG_WL(K7V, double, double, 0);
             break;
         case K25V:
-            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K25V, float, float);
-            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K25V, float, __nv_bfloat16);
-            if (a.fdt == DT_F64) STG_WL(K25V, double, double);
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WL(K25V, float, float, 0);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WL(K25V, float, __nv_bfloat16, 0);
+            if (a.fdt == DT_F64) STG_WL(K25V, double, double, 0);
             break;
     }
 #undef STG_WL

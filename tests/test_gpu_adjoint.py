@@ -229,20 +229,26 @@ def test_forward_and_backward_captured_in_one_cuda_graph(kind, fdt, scheme):
         assert np.array_equal(s.last_coef_grad.cpu().numpy(), gc_e)
 
 
-@pytest.mark.parametrize("kind,shape,T,k", [("25pt_var", (44, 31, 27), 11, 0), ("7pt_var", (70, 33, 25), 13, 5),
-                                            ("25pt_var", (30, 26, 22), 9, 9)])
-def test_wavefront_recompute_gives_the_plain_gradients(kind, shape, T, k):
-    """With the grid tuned to the wavefront schedule, the backward pass recomputes each
-    checkpoint segment's states with one temporally blocked pass that writes every time level
-    to its own array; the states, and so the gradients, equal the plain recompute's bit for
-    bit, and they match the FP64 oracle adjoint."""
+@pytest.mark.parametrize("kind,shape,fdt,cdt,T,k", [
+    ("25pt_var", (44, 31, 27), "f32", None, 11, 0), ("7pt_var", (70, 33, 25), "f32", None, 13, 5),
+    ("25pt_var", (30, 26, 22), "f32", None, 9, 9), ("7pt_var", (41, 29, 23), "f64", None, 8, 0),
+    ("25pt_var", (36, 28, 24), "f32", "bf16", 7, 0),
+    ("7pt_var", (300, 520, 6), "f32", None, 8, 4),  # 390 tiles: more (level, tile) pairs than CTAs
+])
+def test_wavefront_backward_gives_the_plain_gradients(kind, shape, fdt, cdt, T, k):
+    """With the grid tuned to the wavefront schedule, the backward pass runs temporally blocked:
+    each checkpoint segment's states are recomputed by one wavefront pass that writes every time
+    level to its own array, and the segment's cotangents by one wavefront pass of transposed
+    steps, each level writing its own cotangent array. Both give the per-step results bit for
+    bit, so the gradients equal the plain-tuned grid's, and they match the FP64 oracle adjoint."""
     from paper_1410_5561_gb300.stencil import Tuning
-    p, s, u0, coefs, target = _grid_and_inputs(kind, shape, "f32", seed=33)
+    p, s, u0, coefs, target = _grid_and_inputs(kind, shape, fdt, cdt, seed=33)
     loss_p, gu_p, gc_p = _autograd_grads(s, u0, coefs, target, T, k)
     R = 4 if kind == "25pt_var" else 1
     s.set_tuning("wavefront", Tuning(4 * R, R, 4, 0))
     loss_w, gu_w, gc_w = _autograd_grads(s, u0, coefs, target, T, k)
     assert loss_w == loss_p
     assert np.array_equal(gu_w, gu_p) and np.array_equal(gc_w, gc_p)
+    tol = 1e-12 if fdt == "f64" else 2e-5
     rl, ru, rc = oracle.adjoint(kind, p.u0, p.coefs, target.double().cpu().numpy(), T)
-    assert _rel(gu_w, ru) <= 2e-5 and _rel(gc_w, rc) <= 2e-5
+    assert _rel(gu_w, ru) <= tol and _rel(gc_w, rc) <= tol

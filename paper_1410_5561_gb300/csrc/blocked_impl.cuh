@@ -115,9 +115,29 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async16_u32(uint32_t s, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// Predicated copy: no branch (so no divergent region) for lanes without a pair.
+__device__ __forceinline__ void cp_async16_if(bool p, uint32_t s, const void* gmem) {
+    asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q cp.async.cg.shared.global [%1], [%2], 16;\n}\n"
+                 ::"r"((unsigned)p), "r"(s), "l"(gmem));
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Predicated 128-bit global store (no branch).
+template <typename TF, int V> struct Stg;
+template <> struct Stg<float, 4> {
+    static __device__ __forceinline__ void st_if(bool p, float* a, const Vec<float, 4>& x) {
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.global.v4.f32 [%1], {%2, %3, %4, %5};\n}\n"
+                     ::"r"((unsigned)p), "l"(a), "f"(x.v[0]), "f"(x.v[1]), "f"(x.v[2]), "f"(x.v[3]));
+    }
+};
+template <> struct Stg<double, 2> {
+    static __device__ __forceinline__ void st_if(bool p, double* a, const Vec<double, 2>& x) {
+        asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q st.global.v2.f64 [%1], {%2, %3};\n}\n"
+                     ::"r"((unsigned)p), "l"(a), "d"(x.v[0]), "d"(x.v[1]));
+    }
+};
 
 // Execution-only barrier across the cluster (the x-tiles of one diamond). It
 // carries no memory ordering: it only keeps the x-tiles in lockstep so that a
@@ -456,19 +476,21 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     const int npair = M.tpre[ntask];
     uint32_t pa_dst[KT];   // shared address: task row, slot 0, the pair's vector
     uint32_t pa_psb[KT];   // plane stride of the task's ring (bytes)
-    const TF* pa_src[KT];  // the pair's vector of the task row at z = 0 (null: fill)
+    const TF* pa_src[KT];  // the pair's vector of the task row at z = 0 (any valid address: fill)
     int pa_zb0[KT];        // first plane at step 0
     int pa_sl[KT];         // ring slot of the first plane of the next call
     bool pa_ok[KT];
+    bool pa_fill[KT];      // a halo row: Dirichlet value, no load
     {
         int ti = 0;
 #pragma unroll
         for (int j = 0; j < KT; ++j) {
             const int q = tid + j * NT;
             pa_ok[j] = q < npair;
+            pa_fill[j] = true;
             pa_dst[j] = 0;
             pa_psb[j] = 0;
-            pa_src[j] = nullptr;
+            pa_src[j] = P.f[0];
             pa_zb0[j] = 0;
             pa_sl[j] = 0;
             if (!pa_ok[j]) continue;
@@ -480,7 +502,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             pa_dst[j] = smem_u32(ring + M.roff[l] + (y - nlo) * Xs + c * V);
             pa_zb0[j] = -l * d + NF + R;
             pa_sl[j] = pmod(s_begin * NF + pa_zb0[j], Q);
-            if (!M.tfill[ti])
+            pa_fill[j] = M.tfill[ti] != 0;
+            if (!pa_fill[j])
                 pa_src[j] = P.f[(p0 + M.t0 + l) & 1] + L.at(0, y, 0) + (ptrdiff_t)(x0 - EH) + (ptrdiff_t)c * V;
         }
     }
@@ -491,7 +514,29 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     const int fill_hi = fdiv(Nz - 2 * NF - R, NF) + 1;
 
     // produce(s) is called for consecutive s (the ring slots advance by N_F per call)
+    const int gplane32 = (int)gplane;  // a plane has fewer than 2^31 elements (32-bit element index)
+    const bool pa_fast = npair <= KT * NT;
     auto produce = [&](int s) {
+        if constexpr (PERSIST) {
+            if (pa_fast && s >= fill_lo && s < fill_hi) {  // block-uniform
+                // steady state: every plane of the call is a real plane of every level, and
+                // halo rows keep the value the ring was filled with, so every thread issues
+                // its pairs' copies predicated, with no branch
+#pragma unroll
+                for (int j = 0; j < KT; ++j) {
+                    const TF* gp = pa_src[j] + (long long)(s * NF + pa_zb0[j]) * gplane32;
+                    const bool live = pa_ok[j] && !pa_fill[j];
+                    int sl = pa_sl[j];
+#pragma unroll
+                    for (int fz = 0; fz < NF; ++fz) {
+                        cp_async16_if(live, pa_dst[j] + (uint32_t)sl * pa_psb[j], gp + (long long)fz * gplane32);
+                        sl = sl + 1 == Q ? 0 : sl + 1;
+                    }
+                    pa_sl[j] = pa_sl[j] + NF >= Q ? pa_sl[j] + NF - Q : pa_sl[j] + NF;
+                }
+                return;
+            }
+        }
         VT hvv;
 #pragma unroll
         for (int e = 0; e < V; ++e) hvv.v[e] = hv;
@@ -501,7 +546,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                 const int z0 = s * NF + pa_zb0[j];
                 int sl = pa_sl[j];
                 if (z0 >= 0 && z0 + NF <= Nz) {  // every plane of the call is a real plane
-                    if (pa_src[j] != nullptr) {
+                    if (!pa_fill[j]) {
                         const TF* gp = pa_src[j] + (size_t)z0 * gplane;
 #pragma unroll
                         for (int fz = 0; fz < NF; ++fz) {
@@ -522,7 +567,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                         const uint32_t dst = pa_dst[j] + (uint32_t)sl * pa_psb[j];
                         sl = sl + 1 == Q ? 0 : sl + 1;
                         if (z < 0 || z >= Nz) continue;
-                        if (pa_src[j] == nullptr) Lds<TF, V>::st(dst, hvv);
+                        if (pa_fill[j]) Lds<TF, V>::st(dst, hvv);
                         else cp_async16_u32(dst, pa_src[j] + (size_t)z * gplane);
                     }
                 }
@@ -673,7 +718,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                             }
                         }
                         Lds<TF, V>::st_if(I.wr[i], I.ad[i] + (uint32_t)sc * dPSB, out);
-                        if (I.store[i]) stv<TF, V>(I.gdst + gidx, out);
+                        Stg<TF, V>::st_if(I.store[i], I.gdst + gidx, out);
                     }
                     sc = sc + 1 == Q ? 0 : sc + 1;
                 }

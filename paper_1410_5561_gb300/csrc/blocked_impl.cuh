@@ -257,8 +257,10 @@ struct Item {
     bool hasd[RB];     // row y0+i has a ring row at level l+1
     TF* gdst;          // HBM array receiving u_{t+1}
     uint32_t g0[RB];   // element index of (xg, y0+i, z = 0) (< (R + 1) planes, checked on the host)
+    char* gst[RB];     // address of (xg, y0+i, z = 0) in gdst
     int PS, dPS;       // ring plane strides (elements)
     int zb0;           // z of the item's first plane at step 0 (= -l d)
+    int slz;           // ring slot of the item's first plane at the current step
     int qr;            // vectors available to the right of this lane's vector
     int xg;            // interior x of the lane's element 0
     int nr;            // valid rows (1..RB)
@@ -444,7 +446,10 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             I.g0[i] = I.indom ? (uint32_t)L.at(I.xg, y, 0) : 0u;
         }
         I.gdst = P.f[(p0 + M.t0 + l + 1) & 1];
+#pragma unroll
+        for (int i = 0; i < RB; ++i) I.gst[i] = reinterpret_cast<char*>(I.gdst + I.g0[i]);
         I.zb0 = -l * d;
+        I.slz = pmod(s_begin * NF + I.zb0, Q);
         I.ar = smem_u32(I.rowp);
         I.rq = I.qr < 1 ? I.qr : 1;
 #pragma unroll
@@ -514,7 +519,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
     const int fill_hi = fdiv(Nz - 2 * NF - R, NF) + 1;
 
     // produce(s) is called for consecutive s (the ring slots advance by N_F per call)
-    const int gplane32 = (int)gplane;  // a plane has fewer than 2^31 elements (32-bit element index)
+    const int gplaneB = (int)(gplane * sizeof(TF));  // a plane has fewer than 2^28 elements (checked on the host)
     const bool pa_fast = npair <= KT * NT;
     auto produce = [&](int s) {
         if constexpr (PERSIST) {
@@ -524,12 +529,13 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                 // its pairs' copies predicated, with no branch
 #pragma unroll
                 for (int j = 0; j < KT; ++j) {
-                    const TF* gp = pa_src[j] + (long long)(s * NF + pa_zb0[j]) * gplane32;
+                    const char* const gp = reinterpret_cast<const char*>(pa_src[j]);
+                    const int z0 = s * NF + pa_zb0[j];
                     const bool live = pa_ok[j] && !pa_fill[j];
                     int sl = pa_sl[j];
 #pragma unroll
                     for (int fz = 0; fz < NF; ++fz) {
-                        cp_async16_if(live, pa_dst[j] + (uint32_t)sl * pa_psb[j], gp + (long long)fz * gplane32);
+                        cp_async16_if(live, pa_dst[j] + (uint32_t)sl * pa_psb[j], gp + (long long)(z0 + fz) * gplaneB);
                         sl = sl + 1 == Q ? 0 : sl + 1;
                     }
                     pa_sl[j] = pa_sl[j] + NF >= Q ? pa_sl[j] + NF - Q : pa_sl[j] + NF;
@@ -630,6 +636,8 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
             Item<TF, V, RB>& I = it[kk];
             if (!I.valid) continue;
             const int zb = s * NF + I.zb0;
+            const int slz = I.slz;  // = zb mod Q
+            I.slz = slz + NF >= Q ? slz + NF - Q : slz + NF;
             if constexpr (PERSIST) {
                 // the windows advance every step from the start; planes below 0 are the
                 // Dirichlet value, so the ring is never read below the current plane
@@ -646,7 +654,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                 constexpr uint32_t VB = (uint32_t)(V * XB);
                 const uint32_t XsB = (uint32_t)(Xs * XB);
                 const uint32_t PSB = (uint32_t)(I.PS * XB), dPSB = (uint32_t)(I.dPS * XB);
-                int sc = pmod(zb, Q);
+                int sc = slz;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
                     int sn = sc + R;
@@ -718,12 +726,13 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                             }
                         }
                         Lds<TF, V>::st_if(I.wr[i], I.ad[i] + (uint32_t)sc * dPSB, out);
-                        Stg<TF, V>::st_if(I.store[i], I.gdst + gidx, out);
+                        TF* const gp = reinterpret_cast<TF*>(I.gst[i] + (long long)(zb + f) * gplaneB);
+                        Stg<TF, V>::st_if(I.store[i], gp, out);
                     }
                     sc = sc + 1 == Q ? 0 : sc + 1;
                 }
             }
-            const int s0 = pmod(zb, Q);  // ring slot of plane zb
+            const int s0 = slz;  // ring slot of plane zb
 #pragma unroll
             for (int f = 0; f < NF && !fast; ++f) {
                 const int z = zb + f;
@@ -860,12 +869,13 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     }
                     if (I.active && I.hasd[i]) Lds<TF, V>::st(I.ad[i] + (uint32_t)(sc * I.dPS * XB), out);
                     if (I.store[i]) {
+                        TF* const gp = reinterpret_cast<TF*>(I.gst[i] + (long long)z * gplaneB);
                         if (I.full) {
-                            stv<TF, V>(I.gdst + gidx, out);
+                            stv<TF, V>(gp, out);
                         } else {
 #pragma unroll
                             for (int e = 0; e < V; ++e)
-                                if (I.xg + e < Nx) I.gdst[gidx + e] = out.v[e];
+                                if (I.xg + e < Nx) gp[e] = out.v[e];
                         }
                     }
                 }
@@ -1095,8 +1105,10 @@ struct BlkShape {
 // split into 32-vector chunks, each one item.
 static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps, int xtile);
 
-// The kernel keeps the element index of (x, y, z = 0) in 32 bits.
-static bool index32_ok(const Layout& L) { return (size_t)(L.R + 2) * L.plane() < ((size_t)1 << 32); }
+// The kernel keeps the element index of (x, y, z = 0) and a plane's size in bytes in 32 bits.
+static bool index32_ok(const Layout& L) {
+    return (size_t)(L.R + 2) * L.plane() < ((size_t)1 << 32) && L.plane() < ((size_t)1 << 28);
+}
 
 static BlkShape blk_shape_x(int kind, int fdt, int nx, int dw, int nf, int warps, int xtile) {
     BlkShape s{};

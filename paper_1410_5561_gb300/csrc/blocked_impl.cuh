@@ -654,6 +654,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                 constexpr uint32_t VB = (uint32_t)(V * XB);
                 const uint32_t XsB = (uint32_t)(Xs * XB);
                 const uint32_t PSB = (uint32_t)(I.PS * XB), dPSB = (uint32_t)(I.dPS * XB);
+                (void)dPSB;
                 int sc = slz;
 #pragma unroll
                 for (int f = 0; f < NF; ++f) {
@@ -696,6 +697,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                         const size_t gidx = (size_t)I.g0[i] + zoff;  // in bounds for every lane
                         Vec<TC, V> cv[NC > 0 ? NC : 1];
                         (void)cv;
+                        (void)gidx;
                         if constexpr (NC > 0) {
 #pragma unroll
                             for (int m = 0; m < NC; ++m) cv[m] = ldv_ro<TC, V>(P.C[m] + gidx);
@@ -712,17 +714,32 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                                 asm volatile("prefetch.global.L2 [%0];" ::"l"(P.C[m] + gidx + (size_t)NF * gplane));
                         }
                         VT out;
+                        if constexpr (KIND == K7C && std::is_same<TF, float>::value) {
+                            // packed pairs of points (e, e + 1); the x sums are scalar
+                            const F2 c0p = F2::pack(P.c0, P.c0), c1p = F2::pack(P.c1, P.c1);
 #pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            const TF xp = e + 1 < V ? ctr.v[e + 1 < V ? e + 1 : 0] : xpl;
-                            const TF xm = e > 0 ? ctr.v[e > 0 ? e - 1 : 0] : xm0;
-                            if constexpr (KIND == K7C) {
-                                out.v[e] = upd7c<TF>(P.c0, P.c1, ctr.v[e], xp, xm, yp.v[e], ym.v[e], zp1.v[e], zm1.v[e]);
-                            } else {
-                                TF c[7];
+                            for (int e = 0; e < V; e += 2) {
+                                const float xpb = e + 2 < V ? ctr.v[e + 2 < V ? e + 2 : 0] : xpl;
+                                const float xma = e > 0 ? ctr.v[e > 0 ? e - 1 : 0] : xm0;
+                                const F2 sx = F2::pack(Ar<float>::add(ctr.v[e + 1], xma), Ar<float>::add(xpb, ctr.v[e]));
+                                const F2 r = upd7c_x2(c0p, c1p, F2::pack(ctr.v[e], ctr.v[e + 1]), sx,
+                                                      F2::pack(yp.v[e], yp.v[e + 1]), F2::pack(ym.v[e], ym.v[e + 1]),
+                                                      F2::pack(zp1.v[e], zp1.v[e + 1]), F2::pack(zm1.v[e], zm1.v[e + 1]));
+                                r.unpack(out.v[e], out.v[e + 1]);
+                            }
+                        } else {
 #pragma unroll
-                                for (int m = 0; m < 7; ++m) c[m] = Cvt<TF, TC>::f(cv[m < NC ? m : 0].v[e]);
-                                out.v[e] = upd7v<TF>(c, ctr.v[e], xp, xm, yp.v[e], ym.v[e], zp1.v[e], zm1.v[e]);
+                            for (int e = 0; e < V; ++e) {
+                                const TF xp = e + 1 < V ? ctr.v[e + 1 < V ? e + 1 : 0] : xpl;
+                                const TF xm = e > 0 ? ctr.v[e > 0 ? e - 1 : 0] : xm0;
+                                if constexpr (KIND == K7C) {
+                                    out.v[e] = upd7c<TF>(P.c0, P.c1, ctr.v[e], xp, xm, yp.v[e], ym.v[e], zp1.v[e], zm1.v[e]);
+                                } else {
+                                    TF c[7];
+#pragma unroll
+                                    for (int m = 0; m < 7; ++m) c[m] = Cvt<TF, TC>::f(cv[m < NC ? m : 0].v[e]);
+                                    out.v[e] = upd7v<TF>(c, ctr.v[e], xp, xm, yp.v[e], ym.v[e], zp1.v[e], zm1.v[e]);
+                                }
                             }
                         }
                         Lds<TF, V>::st_if(I.wr[i], I.ad[i] + (uint32_t)sc * dPSB, out);
@@ -820,6 +837,7 @@ __device__ __forceinline__ void run_tile(const GridArgs<TF, TC>& P, const int k,
                     const size_t gidx = (size_t)I.g0[i] + zoff;
                     Vec<TC, V> cv[NC > 0 ? NC : 1];
                     (void)cv;
+                    (void)gidx;
                     if constexpr (NC > 0) {
                         if (I.active && I.indom) {
 #pragma unroll

@@ -68,6 +68,47 @@ __device__ __forceinline__ T upd7c(T c0, T c1, T v, T xp, T xm, T yp, T ym, T zp
     return r;
 }
 
+// Two FP32 lanes in one 64-bit register: sm_100-family packed add / mul / fma,
+// each lane rounded exactly like the scalar operation (round to nearest, no
+// flush), so a packed evaluation gives the scalar one's bits.
+struct F2 {
+    unsigned long long r;
+    static __device__ __forceinline__ F2 pack(float a, float b) {
+        F2 x;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(x.r) : "f"(a), "f"(b));
+        return x;
+    }
+    __device__ __forceinline__ void unpack(float& a, float& b) const {
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+    }
+    static __device__ __forceinline__ F2 add(F2 a, F2 b) {
+        F2 x;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(x.r) : "l"(a.r), "l"(b.r));
+        return x;
+    }
+    static __device__ __forceinline__ F2 mul(F2 a, F2 b) {
+        F2 x;
+        asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(x.r) : "l"(a.r), "l"(b.r));
+        return x;
+    }
+    static __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) {
+        F2 x;
+        asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(x.r) : "l"(a.r), "l"(b.r), "l"(c.r));
+        return x;
+    }
+};
+
+// Listing 1 for the points e and e+1 of a vector, packed: the same operations in
+// the same order as upd7c on each point. sx: the x pair sums (xp + xm), formed
+// by the caller because the x neighbours are not register pairs.
+__device__ __forceinline__ F2 upd7c_x2(F2 c0, F2 c1, F2 v, F2 sx, F2 yp, F2 ym, F2 zp, F2 zm) {
+    F2 r = F2::mul(c0, v);
+    r = F2::fma(c1, sx, r);
+    r = F2::fma(c1, F2::add(yp, ym), r);
+    r = F2::fma(c1, F2::add(zp, zm), r);
+    return r;
+}
+
 // Listing 2: U = C0*V + C1*x+ + C2*x- + C3*y+ + C4*y- + C5*z+ + C6*z-
 template <typename T>
 __device__ __forceinline__ T upd7v(const T* c, T v, T xp, T xm, T yp, T ym, T zp, T zm) {

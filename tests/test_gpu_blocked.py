@@ -44,6 +44,24 @@ def test_blocked_bitwise_equals_plain_r1(kind, shape, fdt, cdt, tn, T):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("kind,shape,fdt,cdt,tn", [
+    ("7pt_const", (128, 30, 22), "f32", None, Tuning(8, 2, 16, 28)),
+    ("7pt_const", (128, 30, 22), "f32", None, Tuning(6, 1, 8, 60)),
+    ("7pt_const", (256, 19, 16), "f32", None, Tuning(8, 2, 16, 100)),
+    ("7pt_var", (96, 26, 18), "f32", None, Tuning(8, 2, 16, 20)),
+    ("7pt_var", (96, 26, 18), "f32", "bf16", Tuning(4, 2, 8, 44)),
+    ("7pt_const", (64, 20, 14), "f64", None, Tuning(6, 2, 16, 24)),
+])
+@pytest.mark.parametrize("T", [2, 9])
+def test_blocked_steady_state_path_bitwise(kind, shape, fdt, cdt, tn, T):
+    """x sizes that are multiples of the vector width, so that whole warps take the
+    radius-1 steady-state path (no lane straddles the grid's x boundary)."""
+    p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=15, halo=0.75)
+    a = _run(p, T, "plain")
+    b = _run(p, T, "blocked", tn)
+    assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("tn", R4_TUNINGS, ids=lambda t: f"dw{t.dw}nf{t.nf}w{t.warps}x{t.xtile}")
 @pytest.mark.parametrize("shape,fdt,cdt", [((29, 35, 21), "f32", None), ((18, 25, 14), "f64", None),
                                            ((27, 33, 19), "f32", "bf16")])

@@ -153,7 +153,11 @@ int stencil_set_field(stencil_t h, const void* src, double halo_value, int where
  * sweeps z chunks of nf planes (nf >= R) two chunks behind level l-1, on xy
  * tiles of 32 vectors by `warps` rows (4, 8 or 16, >= R), the CTAs waiting on
  * bounded completion flags; xtile = 2 copies every load two planes ahead into
- * shared memory where nf >= R + 2 and it fits, 0 does not; NULL: h = 2,
+ * shared memory where nf >= R + 2 and it fits, 0 does not; xtile = 4 (25-point
+ * stencil, FP32 field, 8 rows) stages whole tile planes (the field with its
+ * halos, the 13 coefficient planes) in shared memory with tensor copies issued
+ * by one producer warp, where every (level, tile) CTA fits on the GPU at once
+ * (else the column walk runs); NULL: h = 2,
  * 8-plane chunks, 8 rows, no copies ahead; needs a bound workspace, else
  * STENCIL_EINVAL; bit-identical to the plain sweep), or
  * STENCIL_BLOCKED with *tuning (NULL: library default: D_w = 8R, N_F = 2 where it
@@ -238,6 +242,12 @@ size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning);
 
 /* Number of kernels this handle has launched so far (sweeps, fills), into *out. */
 int stencil_launch_count(stencil_t h, long long* out);
+
+/* Number of STENCIL_WAVEFRONT passes (Section II-A's thread group, see
+ * stencil_set_tuning) this handle has run with tile copies into shared memory
+ * (tuning xtile = 4), into *out; the passes that fell back to the column walk
+ * are not counted. */
+int stencil_tile_copy_passes(stencil_t h, long long* out);
 
 /* Measurement support, no counterpart in the paper: time a grid-filling kernel
  * of independent dependent-FMA chains in dtype (STENCIL_F32 or STENCIL_F64) on

@@ -28,6 +28,7 @@ struct stencil_grid {
     int plain_prefetch;  // plain sweep's prefetch depth (0 or 2)
     bool tune_set;
     long long launches;
+    long long tile_passes;  // wavefront passes run with tile copies into shared memory
     bool halo_ok;        // both bound field arrays hold `halo` in every non-interior cell
     bool status_armed;   // the workspace's status word has been zeroed since bind / set_field
     PersistCtl ctl;      // dependency-wait limit and stall hook of the persistent schedule
@@ -149,6 +150,7 @@ int stencil_create(stencil_t* out, int kind, int nx, int ny, int nz, int field_d
     h->scheme = STENCIL_PLAIN;
     h->tune_set = false;
     h->launches = 0;
+    h->tile_passes = 0;
     h->halo_ok = false;
     h->status_armed = false;
     h->ctl.spin_limit = 1u << 24;
@@ -302,7 +304,8 @@ int stencil_set_tuning(stencil_t h, int scheme, const stencil_tuning* tuning) {
         WaveTune w{2, R > 8 ? R : 8, 8, 2, 0};  // default: two levels per pass, 8-plane chunks, 8-row tiles
         if (tuning) {
             if (tuning->dw < 2 * R || tuning->dw % (2 * R) != 0) return STENCIL_EINVAL;
-            if (tuning->xtile != 0 && tuning->xtile != 2) return STENCIL_EINVAL;
+            const bool tiles = tuning->xtile == 4 && h->kind == STENCIL_25PT_VAR && h->fdt == STENCIL_F32;
+            if (tuning->xtile != 0 && tuning->xtile != 2 && !tiles) return STENCIL_EINVAL;
             w.h = tuning->dw / (2 * R);
             w.zc = tuning->nf;
             w.by = tuning->warps;
@@ -356,7 +359,7 @@ int stencil_run(stencil_t h, int T) {
     }
     if (h->scheme == STENCIL_WAVEFRONT) {
         cudaError_t e = wave_run(a, h->field, h->parity, T, h->wtune, h->ws, GRID_WORKSPACE_BYTES, h->ctl, h->stream,
-                                 &h->launches);
+                                 &h->launches, &h->tile_passes);
         if (e == cudaErrorInvalidValue) return STENCIL_EINVAL;
         if (e != cudaSuccess) return STENCIL_ECUDA;
     } else if (h->scheme == STENCIL_BLOCKED) {
@@ -544,6 +547,12 @@ size_t stencil_blocked_smem_bytes(stencil_t h, const stencil_tuning* tuning) {
 int stencil_launch_count(stencil_t h, long long* out) {
     if (!h || !out) return STENCIL_EINVAL;
     *out = h->launches;
+    return STENCIL_OK;
+}
+
+int stencil_tile_copy_passes(stencil_t h, long long* out) {
+    if (!h || !out) return STENCIL_EINVAL;
+    *out = h->tile_passes;
     return STENCIL_OK;
 }
 

@@ -89,7 +89,8 @@ constexpr size_t GRID_WORKSPACE_BYTES = size_t(16) << 20;
 // l-1 by `lag` chunks.
 struct WaveTune {
     int h, zc, by, lag;
-    int cp;  // planes of coefficients each thread copies ahead into shared memory (0 or 2)
+    int cp;  // 0; 2: each thread copies its loads two planes ahead into shared memory;
+             // 4: tensor copies of whole tiles into shared memory (25-point, FP32 field)
 };
 // Workspace words (ints) of the wavefront schedule: the status word (shared with the
 // persistent blocked schedule), a flag no unit sets, the unit counter, then one
@@ -105,7 +106,14 @@ cudaError_t wave_run_levels(const SweepArgs& a, void* const* levels, int nlev, c
                             bool transposed = false);
 // T steps in passes of tn.h levels, one launch per pass.
 cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
-                     size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches);
+                     size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches,
+                     long long* tile_passes = nullptr);
+// One forward pass of the 25-point stencil (FP32 field) whose operands are staged in shared
+// memory by tensor copies (wave_tma.cu); levels[l] -> levels[l + 1], h levels alternating between
+// two arrays. cudaErrorNotReady when the grid, tuning or device does not allow it (the caller
+// then runs the column-walk form).
+cudaError_t wave_tma_pass(const SweepArgs& a, void* const* levels, int h, const WaveTune& tn, int* ws,
+                          const PersistCtl& ctl, cudaStream_t st, long long* launches);
 
 // Shared-memory bytes the blocked kernel needs for a tuning (0 if infeasible).
 size_t blocked_smem_bytes(const SweepArgs& a, const BlockedTune& tune);

@@ -393,7 +393,8 @@ static cudaError_t wave_pass_any(const SweepArgs& a, void* const* lvl, const Wav
 
 template <int KIND, typename TF, typename TC>
 static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
-                              size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches) {
+                              size_t ws_bytes, const PersistCtl& ctl, cudaStream_t st, long long* launches,
+                              long long* tile_passes) {
     int* w = static_cast<int*>(ws);
     for (int t = 0; t < T;) {
         const int h = T - t < tn.h ? T - t : tn.h;
@@ -403,6 +404,15 @@ static cudaError_t wave_run_t(const SweepArgs& a, void* const field[2], int p0, 
         cudaError_t e = cudaErrorInvalidValue;
         void* lvl[WAVE_MAXLV + 1];
         for (int l = 0; l <= h; ++l) lvl[l] = field[(p0 + t + l) & 1];
+        if (tn.cp == 4) {  // tile copies into shared memory where the grid and device allow them
+            e = wave_tma_pass(a, lvl, h, tn, w, ctl, st, launches);
+            if (e == cudaSuccess) {
+                if (tile_passes) ++*tile_passes;
+                t += h;
+                continue;
+            }
+            if (e != cudaErrorNotReady) return e;
+        }
         if (tn.by == 4) e = wave_pass_any<KIND, TF, TC, 4>(a, lvl, sh, w, ctl, st, launches);
         else if (tn.by == 8) e = wave_pass_any<KIND, TF, TC, 8>(a, lvl, sh, w, ctl, st, launches);
         else if (tn.by == 16) e = wave_pass_any<KIND, TF, TC, 16>(a, lvl, sh, w, ctl, st, launches);
@@ -419,30 +429,31 @@ size_t wave_workspace_bytes(const SweepArgs& a, const WaveTune& tn) {
 }
 
 cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, const WaveTune& tn, void* ws,
-                     size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches) {
+                     size_t ws_bytes, const PersistCtl& ctl, cudaStream_t s, long long* launches,
+                     long long* tile_passes) {
     if (T <= 0 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
     if (!ws) return cudaErrorInvalidValue;
     switch (a.kind) {
         case K7C:
-            if (a.fdt == DT_F32) return wave_run_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+            if (a.fdt == DT_F32) return wave_run_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             if (a.fdt == DT_F64)
-                return wave_run_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             break;
         case K7V:
             if (a.fdt == DT_F32 && a.cdt == DT_F32)
-                return wave_run_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return wave_run_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             if (a.fdt == DT_F64)
-                return wave_run_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             break;
         case K25V:
             if (a.fdt == DT_F32 && a.cdt == DT_F32)
-                return wave_run_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return wave_run_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             if (a.fdt == DT_F64)
-                return wave_run_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches);
+                return wave_run_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
             break;
     }
     return cudaErrorInvalidValue;

@@ -248,6 +248,12 @@ class Stencil:
         C.call("stencil_launch_count", self._h, ctypes.byref(n))
         return int(n.value)
 
+    def tile_copy_passes(self) -> int:
+        """Wavefront passes run with tile copies into shared memory (tuning xtile = 4)."""
+        n = ctypes.c_longlong(0)
+        C.call("stencil_tile_copy_passes", self._h, ctypes.byref(n))
+        return int(n.value)
+
     def sync(self):
         """Wait for the grid's stream; raises on a CUDA error or a device-side timeout."""
         C.call("stencil_sync", self._h)

@@ -148,3 +148,86 @@ def test_wavefront_unit_form_when_streams_outnumber_resident_ctas():
     s.inject_stall(3000)
     s.run(2)
     assert STATUS[s.status()] == "STENCIL_ETIMEOUT"
+
+
+# Tile copies (xtile = 4): the 25-point stencil with an FP32 field, 8-row tiles, whole tile
+# planes staged in shared memory by tensor copies (one CTA per level and tile).
+TILE_WAVE = [Tuning(16, 4, 8, 4), Tuning(16, 8, 8, 4), Tuning(24, 5, 8, 4), Tuning(8, 16, 8, 4)]
+
+
+@pytest.mark.parametrize("tn", TILE_WAVE, ids=lambda t: f"dw{t.dw}zc{t.nf}")
+@pytest.mark.parametrize("shape,cdt", [((141, 35, 27), None), ((27, 33, 19), "bf16"), ((256, 16, 12), None),
+                                       ((130, 9, 5), "bf16"), ((300, 20, 17), None)])
+@pytest.mark.parametrize("T", [1, 3, 9])
+def test_tile_copy_wavefront_bitwise_equals_plain(shape, cdt, tn, T):
+    p = Problem("25pt_var", *shape, fdt="f32", cdt=cdt, seed=28, halo=-0.375)
+    assert np.array_equal(_run(p, T, "plain"), _run(p, T, "wavefront", tn))
+
+
+@pytest.mark.parametrize("cdt", [None, "bf16"])
+def test_tile_copy_wavefront_runs_the_tile_copy_kernel(cdt):
+    """The tile-copy pass is the kernel that runs when every (level, tile) CTA fits (and
+    not the column walk it falls back to otherwise)."""
+    p = Problem("25pt_var", 200, 40, 24, fdt="f32", cdt=cdt, seed=29)
+    s = p.make()
+    s.set_tuning("wavefront", Tuning(16, 8, 8, 4))
+    s.run(4)
+    assert s.tile_copy_passes() == 2  # two passes of two levels
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 4, "plain"))
+    # a tiling with more (level, tile) CTAs than fit at once falls back to the column walk
+    q = Problem("25pt_var", 1024, 400, 6, fdt="f32", cdt=cdt, seed=29)
+    w = q.make()
+    w.set_tuning("wavefront", Tuning(16, 4, 8, 4))
+    w.run(2)
+    assert w.tile_copy_passes() == 0
+    assert np.array_equal(w.get_field().cpu().numpy(), _run(q, 2, "plain"))
+
+
+@pytest.mark.parametrize("cdt", [None, "bf16"])
+def test_tile_copy_wavefront_matches_oracle(cdt):
+    p = Problem("25pt_var", 150, 29, 22, fdt="f32", cdt=cdt, seed=30)
+    got = _run(p, 6, "wavefront", Tuning(16, 4, 8, 4)).astype(np.float64)
+    ref = p.oracle(6)
+    assert oracle.step_normalised_l2(got, ref, 6) <= step_tol("f32")
+    assert np.max(np.abs(got - ref)) <= p.elementwise_tol(6)
+
+
+def test_tile_copy_wavefront_degenerate_shapes():
+    for shape in [(1, 1, 1), (5, 2, 3), (9, 3, 40), (300, 1, 5), (3, 70, 2), (129, 8, 1)]:
+        p = Problem("25pt_var", *shape, fdt="f32", seed=31, halo=0.5)
+        assert np.array_equal(_run(p, 5, "plain"), _run(p, 5, "wavefront", Tuning(16, 4, 8, 4))), shape
+
+
+def test_tile_copy_wavefront_timeout_reported_and_graph_captured():
+    """A level-0 CTA made to wait on a flag nothing sets ends the pass with the status word set;
+    after a new field the same tuning runs exactly, also replayed from a CUDA graph."""
+    import torch
+    from paper_1410_5561_gb300._lib import STATUS, StencilError
+    p = Problem("25pt_var", 200, 40, 36, fdt="f32", seed=32, halo=0.25)
+    s = p.make()
+    s.set_tuning("wavefront", Tuning(16, 4, 8, 4))
+    s.set_wait_limit(2000)
+    s.inject_stall(3)
+    s.run(2)
+    assert STATUS[s.status()] == "STENCIL_ETIMEOUT"
+    with pytest.raises(StencilError):
+        s.sync()
+    s.inject_stall(-1)
+    s.set_wait_limit(1 << 24)
+    u0, _ = p.torch_inputs("cuda")
+    s.set_field(u0, halo=p.halo)
+    s.run(2)
+    torch.cuda.synchronize()
+    g = s.capture(4)
+    g.replay()
+    torch.cuda.synchronize()
+    assert s.status() == 0
+    assert np.array_equal(s.get_field().cpu().numpy(), _run(p, 6, "plain"))
+
+
+def test_tile_copy_option_only_for_the_25_point_fp32_field():
+    from paper_1410_5561_gb300._lib import StencilError
+    for kind, fdt in [("7pt_var", "f32"), ("25pt_var", "f64"), ("7pt_const", "f32")]:
+        s = Problem(kind, 40, 40, 40, fdt=fdt, seed=1).make()
+        with pytest.raises(StencilError):
+            s.set_tuning("wavefront", Tuning(16 if kind == "25pt_var" else 4, 4, 8, 4))

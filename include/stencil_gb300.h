@@ -249,6 +249,16 @@ int stencil_launch_count(stencil_t h, long long* out);
  * are not counted. */
 int stencil_tile_copy_passes(stencil_t h, long long* out);
 
+/* Host transfers, no counterpart in the paper: copy `bytes` from src to dst with
+ * the SMs' own 16-byte loads and stores, by `ctas` CTAs (1..1024) of 1024 threads,
+ * asynchronously on cuda_stream. Either pointer may be device memory or
+ * page-locked host memory (both are addressable by the GPU). With few CTAs the
+ * copy streams host memory over the link on the SMs a running sweep leaves free,
+ * instead of on the copy engines. Both pointers 16-byte aligned and bytes a
+ * multiple of 16, else STENCIL_EINVAL; the caller keeps both buffers alive and
+ * untouched until the stream has passed the copy. */
+int stencil_copy(void* dst, const void* src, size_t bytes, int ctas, void* cuda_stream);
+
 /* Measurement support, no counterpart in the paper: time a grid-filling kernel
  * of independent dependent-FMA chains in dtype (STENCIL_F32 or STENCIL_F64) on
  * cuda_stream and return its duration (*seconds) and flop count (*flops, two

@@ -61,6 +61,7 @@ SIGNATURES = [
     ("stencil_blocked_smem_bytes", ctypes.c_size_t, [_H, ctypes.POINTER(stencil_tuning)]),
     ("stencil_launch_count", _I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     ("stencil_tile_copy_passes", _I, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    ("stencil_copy", _I, [_P, _P, ctypes.c_size_t, _I, _P]),
     ("stencil_adjoint_workspace_bytes", ctypes.c_size_t, [_H, _I, _I]),
     ("stencil_run_checkpointed", _I, [_H, _I, _I, _P, ctypes.c_size_t]),
     ("stencil_run_adjoint", _I, [_H, _I, _I, _P, _P, ctypes.POINTER(_P), _P, ctypes.c_size_t]),

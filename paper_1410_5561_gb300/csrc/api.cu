@@ -556,6 +556,13 @@ int stencil_tile_copy_passes(stencil_t h, long long* out) {
     return STENCIL_OK;
 }
 
+int stencil_copy(void* dst, const void* src, size_t bytes, int ctas, void* cuda_stream) {
+    if (!dst || !src || ctas < 1 || ctas > 1024) return STENCIL_EINVAL;
+    if ((((uintptr_t)dst | (uintptr_t)src | bytes) & 15u) != 0) return STENCIL_EINVAL;
+    if (dense_copy(dst, src, bytes, ctas, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return STENCIL_ECUDA;
+    return STENCIL_OK;
+}
+
 // ------------------------------------------------------------------ batch
 
 struct stencil_batch {

@@ -42,6 +42,9 @@ cudaError_t plain_step(const SweepArgs& a, const void* src, void* dst, cudaStrea
 
 // Fill n elements of dtype dt at p with value v.
 cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s);
+// bytes (a multiple of 16, both pointers 16-byte aligned) from src to dst by `ctas` CTAs of
+// 1024 threads; either side may be page-locked host memory.
+cudaError_t dense_copy(void* dst, const void* src, size_t bytes, int ctas, cudaStream_t s);
 // Dense interior rows <-> padded layout (src/dst device or device-mapped host pointers).
 cudaError_t copy_rows(const Layout& L, int eb, const void* src, void* dst, bool to_padded, cudaStream_t s);
 

@@ -200,6 +200,31 @@ cudaError_t copy_rows(const Layout& L, int eb, const void* src, void* dst, bool 
     return cudaGetLastError();
 }
 
+// Dense copy by the SMs' own loads and stores, with few CTAs: each thread keeps DC_U
+// independent 16-byte loads in flight, so a handful of SMs can stream host memory over the
+// link while the other SMs run a sweep.
+constexpr int DC_U = 8;
+__global__ void __launch_bounds__(1024) dense_copy_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                          size_t n) {
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (DC_U - 1) * stride < n; i += DC_U * stride) {
+        uint4 v[DC_U];
+#pragma unroll
+        for (int u = 0; u < DC_U; ++u) v[u] = src[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < DC_U; ++u) dst[i + u * stride] = v[u];
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
+cudaError_t dense_copy(void* dst, const void* src, size_t bytes, int ctas, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    dense_copy_kernel<<<(unsigned)ctas, 1024, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst),
+                                                      bytes / 16);
+    return cudaGetLastError();
+}
+
 cudaError_t fill_value(void* p, size_t n, int dt, double v, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     unsigned blocks = (unsigned)((n + 255) / 256);

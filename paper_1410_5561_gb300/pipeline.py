@@ -27,29 +27,40 @@ CUDA starts; ``bench.py`` does.
 The copy engines' rate to page-locked host memory differs between machines of the same kind
 (measured 200 GB/s per direction on some GB300 machines, 40-70 GB/s on others), while the
 library's copy kernel, which keeps many SM loads in flight, held about 200 GB/s on all of
-them. Where the copy engines are slow the staged mode loses to running the jobs one by one
-with the copy kernel ("direct" mode: set_field / run / get_field from and to the host). With
-``mode="auto"`` the first call times both on its first input (three staged jobs, whose
-steady-state cost per job is the distance between consecutive sweeps, against one direct
-job) and keeps the faster; ``calibration`` records the figures.
+them. Three modes:
+
+- "staged": the staging scheme above with the copy engines (DMA) moving the host data;
+- "overlap": the same scheme with the library's SM copy (``stencil_copy``) on the transfer
+  streams, limited to ``copy_ctas`` CTAs so that it runs on the SMs the persistent sweep
+  leaves free (a 1024^3 sweep places 15 clusters of 9 CTAs on 135 of the 152 SMs);
+- "direct": the jobs one by one, set_field / run / get_field from and to the host with the
+  library's copy kernel on all SMs.
+
+With ``mode="auto"`` the first call times the three on its first input (three staged or
+overlapped jobs, whose steady-state cost per job is the distance between consecutive sweeps,
+against one direct job) and keeps the fastest; ``calibration`` records the figures.
 """
 from __future__ import annotations
 
+import ctypes
+
 import torch
 
+from . import _lib as C
 from .stencil import Stencil
 
 
 class Pipeline:
-    MODES = ("auto", "staged", "direct")
+    MODES = ("auto", "staged", "overlap", "direct")
 
-    def __init__(self, grid: Stencil, T: int, halo: float = 0.0, mode: str = "auto"):
+    def __init__(self, grid: Stencil, T: int, halo: float = 0.0, mode: str = "auto", copy_ctas: int = 16):
         if mode not in self.MODES:
             raise ValueError(f"mode must be one of {self.MODES}")
         self.grid = grid
         self.T = int(T)
         self.halo = float(halo)
         self.mode = mode
+        self.copy_ctas = int(copy_ctas)
         self.calibration = None
         self._trace = None
         dev = grid.device
@@ -77,20 +88,23 @@ class Pipeline:
             self._calibrate(inputs[0], outputs[0])
         if self.mode == "direct":
             return self._run_direct(inputs, outputs, trace)
-        return self._run_staged(inputs, outputs, trace)
+        return self._run_staged(inputs, outputs, trace, sm_copies=self.mode == "overlap")
 
     def _calibrate(self, src: torch.Tensor, dst: torch.Tensor):
         import time
         dev = self.grid.device
-        self._run_staged([src] * 3, [dst] * 3, trace=True).synchronize()
-        tl = self.timeline()
-        staged = (tl[2]["run"] - tl[0]["run"]) / 2
+        cost = {}
+        for mode in ("staged", "overlap"):
+            self._run_staged([src] * 3, [dst] * 3, trace=True, sm_copies=mode == "overlap").synchronize()
+            tl = self.timeline()
+            cost[mode] = (tl[2]["run"] - tl[0]["run"]) / 2
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         self._run_direct([src], [dst], False).synchronize()
-        direct = 1e3 * (time.perf_counter() - t0)
-        self.mode = "staged" if staged <= direct else "direct"
-        self.calibration = {"staged_ms_per_job": staged, "direct_ms_per_job": direct, "chosen": self.mode}
+        cost["direct"] = 1e3 * (time.perf_counter() - t0)
+        self.mode = min(cost, key=cost.get)
+        self.calibration = {f"{m}_ms_per_job": v for m, v in cost.items()}
+        self.calibration["chosen"] = self.mode
         if self.mode == "direct":  # the staging arrays are not needed any more
             self.staging_in = self.staging_out = None
 
@@ -112,7 +126,18 @@ class Pipeline:
         self._t0 = t0
         return g.stream.record_event()
 
-    def _run_staged(self, inputs, outputs, trace: bool):
+    def _copy(self, dst: torch.Tensor, src: torch.Tensor, stream, sm_copies: bool):
+        """dst <- src (same shape) on `stream`: the library's SM copy with copy_ctas CTAs, or the
+        copy engines (also for sizes the SM copy does not take: not a multiple of 16 bytes)."""
+        nbytes = src.numel() * src.element_size()
+        if sm_copies and nbytes % 16 == 0 and dst.data_ptr() % 16 == 0 and src.data_ptr() % 16 == 0:
+            C.call("stencil_copy", ctypes.c_void_p(dst.data_ptr()), ctypes.c_void_p(src.data_ptr()),
+                   ctypes.c_size_t(nbytes), self.copy_ctas, ctypes.c_void_p(stream.cuda_stream))
+        else:
+            with torch.cuda.stream(stream):
+                dst.copy_(src, non_blocking=True)
+
+    def _run_staged(self, inputs, outputs, trace: bool, sm_copies: bool = False):
         g = self.grid
         if self.staging_in is None:
             shape = (g.nz, g.ny, g.nx)
@@ -134,7 +159,7 @@ class Pipeline:
                 if consumed is not None:
                     self.h2d.wait_event(consumed)
                 ev["h2d"] = self._mark(self.h2d)
-                self.staging_in.copy_(src, non_blocking=True)
+                self._copy(self.staging_in, src, self.h2d, sm_copies)
                 ev["h2d_end"] = self._mark(self.h2d)
                 loaded = self.h2d.record_event()
             self.compute.wait_event(loaded)
@@ -151,7 +176,7 @@ class Pipeline:
             with torch.cuda.stream(self.d2h):
                 self.d2h.wait_event(ready)
                 ev["d2h"] = self._mark(self.d2h)
-                dst.copy_(self.staging_out, non_blocking=True)
+                self._copy(dst, self.staging_out, self.d2h, sm_copies)
                 ev["end"] = self._mark(self.d2h)
                 emptied = last = self.d2h.record_event()
             if self._trace is not None:

@@ -32,7 +32,7 @@ def _sequential(p, jobs, T, scheme, tn, halo):
     ("25pt_var", (29, 24, 22), "f64", None, "plain", None),
 ])
 @pytest.mark.parametrize("T", [1, 8])
-@pytest.mark.parametrize("mode", ["staged", "direct", "auto"])
+@pytest.mark.parametrize("mode", ["staged", "overlap", "direct", "auto"])
 def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T, mode):
     p = Problem(kind, *shape, fdt=fdt, cdt=cdt, seed=21, halo=0.25)
     tdt = {"f32": torch.float32, "f64": torch.float64}[fdt]
@@ -45,8 +45,8 @@ def test_pipeline_equals_jobs_one_by_one(kind, shape, fdt, cdt, scheme, tn, T, m
     outs = [torch.empty_like(u).pin_memory() for u in jobs]
     pipe = Pipeline(s, T, halo=p.halo, mode=mode)
     pipe.run(jobs, outs).synchronize()
-    if mode == "auto":  # calibrated once on the first input, then one of the two modes
-        assert pipe.mode in ("staged", "direct") and pipe.calibration["chosen"] == pipe.mode
+    if mode == "auto":  # calibrated once on the first input, then one of the three modes
+        assert pipe.mode in ("staged", "overlap", "direct") and pipe.calibration["chosen"] == pipe.mode
     for a, b in zip(outs, want):
         assert torch.equal(a, b)
     # a second pass through the same pipeline (halo kept, grid reused) gives the same
@@ -113,3 +113,35 @@ def test_async_host_transfer_rejects_pageable_and_device_memory():
     with pytest.raises(C.StencilError):
         C.call("stencil_set_coeffs", s._h, c, None, C.STENCIL_HOST_ASYNC)
     assert np.isfinite(s.get_field().cpu().numpy()).all()
+
+
+def test_sm_copy_between_host_and_device():
+    """stencil_copy moves bytes between page-locked host and device memory in both directions
+    and device to device, with any CTA count, and rejects unaligned pointers or sizes."""
+    import ctypes
+    from paper_1410_5561_gb300 import _lib as C
+    from paper_1410_5561_gb300._lib import StencilError
+    g = torch.Generator().manual_seed(9)
+    n = 3 * 1024 * 1024 + 12  # not a multiple of the copy's unrolled stride
+    host = torch.randint(-2**31, 2**31 - 1, (n,), generator=g, dtype=torch.int32).pin_memory()
+    dev = torch.empty(n, dtype=torch.int32, device="cuda")
+    back = torch.empty(n, dtype=torch.int32).pin_memory()
+    st = torch.cuda.current_stream()
+    for ctas in (1, 7, 64):
+        dev.zero_()
+        back.zero_()
+        C.call("stencil_copy", ctypes.c_void_p(dev.data_ptr()), ctypes.c_void_p(host.data_ptr()),
+               ctypes.c_size_t(4 * n), ctas, ctypes.c_void_p(st.cuda_stream))
+        dev2 = torch.empty_like(dev)
+        C.call("stencil_copy", ctypes.c_void_p(dev2.data_ptr()), ctypes.c_void_p(dev.data_ptr()),
+               ctypes.c_size_t(4 * n), ctas, ctypes.c_void_p(st.cuda_stream))
+        C.call("stencil_copy", ctypes.c_void_p(back.data_ptr()), ctypes.c_void_p(dev2.data_ptr()),
+               ctypes.c_size_t(4 * n), ctas, ctypes.c_void_p(st.cuda_stream))
+        torch.cuda.synchronize()
+        assert torch.equal(back, host)
+    for dst, src, nbytes, ctas in [(dev.data_ptr() + 4, host.data_ptr(), 16, 4),   # unaligned destination
+                                   (dev.data_ptr(), host.data_ptr(), 20, 4),       # size not a multiple of 16
+                                   (dev.data_ptr(), host.data_ptr(), 16, 0)]:      # no CTA
+        with pytest.raises(StencilError):
+            C.call("stencil_copy", ctypes.c_void_p(dst), ctypes.c_void_p(src), ctypes.c_size_t(nbytes), ctas,
+                   ctypes.c_void_p(st.cuda_stream))

@@ -521,7 +521,7 @@ def run_ours(args):
                    "d2h_bytes_per_step": nbytes, "steps": ks}
         pipe = Pipeline(s, T, halo=0.0, mode="auto")
         pipe.run([host_in] * 2, host_out).synchronize()  # warm-up and the mode's calibration
-        kp = max(6, args.steps)  # jobs in flight amortise the first copy in and the last copy out
+        kp = max(8, args.steps)  # jobs in flight amortise the first copy in and the last copy out
         passes, traces = [], []
         for _ in range(3):  # the host link is shared with the node's other work: median of 3 passes
             barrier()

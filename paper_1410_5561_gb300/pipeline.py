@@ -32,7 +32,10 @@ them. Three modes:
 - "staged": the staging scheme above with the copy engines (DMA) moving the host data;
 - "overlap": the same scheme with the library's SM copy (``stencil_copy``) on the transfer
   streams, limited to ``copy_ctas`` CTAs so that it runs on the SMs the persistent sweep
-  leaves free (a 1024^3 sweep places 15 clusters of 9 CTAs on 135 of the 152 SMs);
+  leaves free (a 1024^3 sweep places 15 clusters of 9 CTAs on 135 of the 152 SMs). Four CTAs
+  move a 1024^3 FP32 field in about 30 ms; the host traffic they drive slows the sweep beside
+  them by about 18 % (116 -> 137 ms, measured with 4 to 24 CTAs), which the copy engines do not,
+  so this mode wins only where the copy engines are slow;
 - "direct": the jobs one by one, set_field / run / get_field from and to the host with the
   library's copy kernel on all SMs.
 
@@ -53,7 +56,7 @@ from .stencil import Stencil
 class Pipeline:
     MODES = ("auto", "staged", "overlap", "direct")
 
-    def __init__(self, grid: Stencil, T: int, halo: float = 0.0, mode: str = "auto", copy_ctas: int = 16):
+    def __init__(self, grid: Stencil, T: int, halo: float = 0.0, mode: str = "auto", copy_ctas: int = 4):
         if mode not in self.MODES:
             raise ValueError(f"mode must be one of {self.MODES}")
         self.grid = grid

@@ -161,7 +161,8 @@ int stencil_set_field(stencil_t h, const void* src, double halo_value, int where
  * 8-plane chunks, 8 rows, no copies ahead; needs a bound workspace, else
  * STENCIL_EINVAL; bit-identical to the plain sweep), or
  * STENCIL_BLOCKED with *tuning (NULL: library default: D_w = 8R, N_F = 2 where it
- * fits, 16 warps for R = 1, the widest x tile whose rows fit one warp of vectors), or
+ * fits (1 for the 7-point variable stencil with FP32 coefficients), 16 warps for
+ * R = 1, the widest x tile whose rows fit one warp of vectors), or
  * STENCIL_AUTO (plain for FP64 fields and the 25-point stencil, where the plain sweep
  * measured faster on GB300; else the default blocked tuning when it fits, else plain).
  * Returns STENCIL_ENOSMEM / STENCIL_EINVAL for an infeasible blocked tuning. */

@@ -52,7 +52,8 @@ static SweepArgs args_of(const stencil_grid* h) {
     return a;
 }
 
-// Default blocked tuning: D_w = 8 (R = 1) or 16 (R = 4), one frontline, 16 (8)
+// Default blocked tuning: D_w = 8 (R = 1) or 16 (R = 4), two frontlines (one for the
+// 7-point variable stencil with FP32 coefficients, measured faster on GB300), 16 (8)
 // warps, x tiles sized so that a tile row plus its trapezoid overlap is one warp
 // of vectors; D_w is halved until the rings fit the shared-memory opt-in limit.
 static BlockedTune default_tune(const stencil_grid* h) {
@@ -60,7 +61,7 @@ static BlockedTune default_tune(const stencil_grid* h) {
     int R = kind_radius(h->kind);
     int eb = dtype_bytes(h->fdt);
     t.dw = R == 1 ? 8 : 16;
-    t.nf = 2;
+    t.nf = (h->kind == STENCIL_7PT_VAR && h->fdt == STENCIL_F32 && h->cdt == STENCIL_F32) ? 1 : 2;
     t.warps = R == 1 ? 16 : 8;
     {
         // widest x tile whose bottom level (tile plus trapezoid overlap) fits one warp of vectors
@@ -68,6 +69,22 @@ static BlockedTune default_tune(const stencil_grid* h) {
         int ov = ((R * (t.dw / R - 2) + V - 1) / V) * V;
         t.xtile = 32 * V - 2 * ov;
         if (t.xtile < V) t.xtile = V;
+        // then the narrowest one that keeps the number of x tiles per row (less overlap work):
+        // with R = 1 the first and last tiles are wider by their one-sided overlap
+        const int nx = h->L.nx, lt = t.dw / R - 1;
+        const int ove = lt > 1 ? ((R * (lt - 1) + V - 1) / V) * V : 0;
+        auto tiles = [&](int xt) {
+            if (nx <= xt) return 1;
+            if (R != 1) return (nx + xt - 1) / xt;
+            const int xe = xt + ove;
+            return nx <= 2 * xe ? 2 : 2 + (nx - 2 * xe + xt - 1) / xt;
+        };
+        const int n0 = tiles(t.xtile);
+        for (int xt = V; xt < t.xtile; xt += V)
+            if (tiles(xt) == n0) {
+                t.xtile = xt;
+                break;
+            }
     }
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);

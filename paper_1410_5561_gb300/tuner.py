@@ -96,7 +96,7 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
     fdt = _DT_NAME[s.dtype]
     cdt = _DT_NAME[s.coef_dtype]
     # measured order of merit on GB300: one item per warp, D_w near 8R (the largest width whose
-    # rings leave room for 16 warps), 16 warps, two frontlines, then the share of computed x
+    # rings leave room for 16 warps), 16 warps, the cheaper frontline count, then the share of computed x
     # columns that are useful (each x tile computes whole 32-vector chunks of its row, overlap
     # included); the model code balance (Eq. 5) breaks ties
     def chunks(t):
@@ -112,7 +112,7 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
         # Eq. 3): with R = 1 each warp keeps its items' z-windows in registers, and tunings
         # that give a warp more than one item spill under the 128-register cap of 512-thread
         # CTAs (measured 2.4-11x slower at 512^3; they stay as a last resort)
-        return (r == 1 and items_per_warp(t, r, v) > 1, abs(t.dw - 8 * r), -t.warps, -t.nf,
+        return (r == 1 and items_per_warp(t, r, v) > 1, abs(t.dw - 8 * r), -t.warps, nf_cost(kind, fdt, cdt, t.nf),
                 -round(useful(t), 3), chunks(t), -t.xtile, model.bytes_per_lup(kind, fdt, cdt, "blocked", t.dw))
     out.sort(key=score)
     return out
@@ -122,11 +122,21 @@ def candidates(s: Stencil, nfs=(1, 2), warps=(8, 16), max_dw=None) -> list[Tunin
 # uses, measured on GB300 (2070 MHz): the plain sweep streams at 0.83 of the copy rate, the
 # one-CTA-per-SM diamond kernel at 0.42 of it for every diamond width whose items fit one per
 # warp (D_w = 4, 6, 8 at 512^3: 2.6-2.9 TB/s), and a warp with 2 or 4 items spills (3x and 7x
-# slower); one frontline costs 23 % more per update than two (one CTA barrier per plane).
+# slower); one frontline costs 23 % more per update than two (one CTA barrier per plane), except
+# for the 7-point variable stencil with FP32 coefficients, whose two frontlines wait on their
+# coefficient loads one after the other: there one frontline is 6 % cheaper (215 vs 201 GLUP/s
+# at 384^3, T = 50).
 PLAIN_STREAM = 0.83
 BLOCKED_STREAM = 0.42
 SPILL = {1: 1.0, 2: 3.0, 4: 7.0}
 NF_COST = {1: 1.23, 2: 1.0}
+NF_COST_7PT_VAR_F32 = {1: 0.94, 2: 1.0}
+
+
+def nf_cost(kind: str, fdt: str, cdt: str, nf: int) -> float:
+    """Measured cost factor of N_F frontlines per update (relative to two)."""
+    table = NF_COST_7PT_VAR_F32 if (kind == "7pt_var" and fdt == "f32" and cdt == "f32") else NF_COST
+    return table.get(nf, 1.0)
 HBM_GBS = 6780.0  # GB300 copy bandwidth, used when the caller gives none
 PRUNE = 1.5
 
@@ -162,7 +172,7 @@ def predict(s: Stencil, T: int, scheme: str, t: Tuning | None = None, hbm_gbs: f
     k = items_per_warp(t, r, v)
     k = 1 if k <= 1 else (2 if k <= 2 else 4)
     mem = lups * b / (BLOCKED_STREAM * hbm_gbs * 1e9)
-    return max(mem, alu) / min(1.0, useful) * SPILL[k] * NF_COST.get(t.nf, 1.0)
+    return max(mem, alu) / min(1.0, useful) * SPILL[k] * nf_cost(kind, fdt, cdt, t.nf)
 
 
 def _time_run(s: Stencil, T: int, reps: int) -> float:

@@ -252,8 +252,10 @@ int stencil_tile_copy_passes(stencil_t h, long long* out);
 
 /* Host transfers, no counterpart in the paper: copy `bytes` from src to dst with
  * the SMs' own 16-byte loads and stores, by `ctas` CTAs (1..1024) of 1024 threads,
- * asynchronously on cuda_stream. Either pointer may be device memory or
- * page-locked host memory (both are addressable by the GPU). With few CTAs the
+ * asynchronously on cuda_stream. Either pointer may be device memory of the
+ * current device, managed memory or page-locked host memory mapped for it;
+ * anything else (pageable host memory, another device's memory) is refused
+ * with STENCIL_EINVAL before any access. With few CTAs the
  * copy streams host memory over the link on the SMs a running sweep leaves free,
  * instead of on the copy engines. Both pointers 16-byte aligned and bytes a
  * multiple of 16, else STENCIL_EINVAL; the caller keeps both buffers alive and

@@ -218,6 +218,23 @@ int stencil_bind(stencil_t h, void* field_a, void* field_b, void* const* coef, v
     return STENCIL_OK;
 }
 
+// The address the current device uses for p: device memory of that device, managed memory, or
+// page-locked host memory mapped for it; null for anything else (pageable host memory, another
+// device's memory, not a pointer CUDA knows), which the SM copy must not dereference.
+static void* device_view(const void* p) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev ? const_cast<void*>(p) : nullptr;
+    if (at.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+    if (at.type == cudaMemoryTypeHost) return at.devicePointer;
+    return nullptr;
+}
+
 static cudaError_t copy_interior(const stencil_grid* h, int eb, const void* dense, void* padded, bool to_padded,
                                  bool dma = false) {
     const Layout& L = h->L;
@@ -575,8 +592,11 @@ int stencil_tile_copy_passes(stencil_t h, long long* out) {
 
 int stencil_copy(void* dst, const void* src, size_t bytes, int ctas, void* cuda_stream) {
     if (!dst || !src || ctas < 1 || ctas > 1024) return STENCIL_EINVAL;
-    if ((((uintptr_t)dst | (uintptr_t)src | bytes) & 15u) != 0) return STENCIL_EINVAL;
-    if (dense_copy(dst, src, bytes, ctas, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return STENCIL_ECUDA;
+    void* d = device_view(dst);
+    const void* s = device_view(src);
+    if (!d || !s) return STENCIL_EINVAL;
+    if ((((uintptr_t)d | (uintptr_t)s | bytes) & 15u) != 0) return STENCIL_EINVAL;
+    if (dense_copy(d, s, bytes, ctas, static_cast<cudaStream_t>(cuda_stream)) != cudaSuccess) return STENCIL_ECUDA;
     return STENCIL_OK;
 }
 

@@ -82,3 +82,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         _lib.lib()
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.call("stencil_strerror", 0)
+
+
+def test_sm_copy_refuses_memory_the_device_cannot_address():
+    """stencil_copy checks both pointers before any access: plain host memory (here no GPU at
+    all, or pageable memory on a GPU machine) is refused with STENCIL_EINVAL."""
+    import ctypes
+    from paper_1410_5561_gb300 import _lib as C
+    buf = (ctypes.c_char * 64)()
+    r = C.lib().stencil_copy(ctypes.c_void_p(ctypes.addressof(buf)), ctypes.c_void_p(ctypes.addressof(buf)),
+                             ctypes.c_size_t(64), 4, None)
+    assert C.STATUS[r] == "STENCIL_EINVAL"

@@ -139,7 +139,10 @@ def test_sm_copy_between_host_and_device():
                ctypes.c_size_t(4 * n), ctas, ctypes.c_void_p(st.cuda_stream))
         torch.cuda.synchronize()
         assert torch.equal(back, host)
-    for dst, src, nbytes, ctas in [(dev.data_ptr() + 4, host.data_ptr(), 16, 4),   # unaligned destination
+    pageable = torch.empty(64, dtype=torch.int32)  # not page-locked: refused before any access
+    for dst, src, nbytes, ctas in [(dev.data_ptr(), pageable.data_ptr(), 64, 4),
+                                   (pageable.data_ptr(), dev.data_ptr(), 64, 4),
+                                   (dev.data_ptr() + 4, host.data_ptr(), 16, 4),   # unaligned destination
                                    (dev.data_ptr(), host.data_ptr(), 20, 4),       # size not a multiple of 16
                                    (dev.data_ptr(), host.data_ptr(), 16, 0)]:      # no CTA
         with pytest.raises(StencilError):

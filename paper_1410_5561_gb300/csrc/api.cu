@@ -247,17 +247,10 @@ static cudaError_t copy_interior(const stencil_grid* h, int eb, const void* dens
             return cudaErrorInvalidValue;
         }
         if (at.type != cudaMemoryTypeHost) return cudaErrorInvalidValue;
-    } else if (cudaPointerGetAttributes(&at, dense) == cudaSuccess) {
-        const void* dp = nullptr;
-        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) dp = dense;
-        else if (at.type == cudaMemoryTypeHost) dp = at.devicePointer;
-        if (dp) {
-            cudaError_t e = to_padded ? copy_rows(L, eb, dp, padded, true, h->stream)
-                                      : copy_rows(L, eb, padded, const_cast<void*>(dp), false, h->stream);
-            return e;
-        }
-    } else {
-        cudaGetLastError();  // not a CUDA pointer: clear the error, use the DMA below
+    } else if (const void* dp = device_view(dense)) {
+        // memory this device addresses (another device's memory and pageable memory take the DMA)
+        return to_padded ? copy_rows(L, eb, dp, padded, true, h->stream)
+                         : copy_rows(L, eb, padded, const_cast<void*>(dp), false, h->stream);
     }
     cudaMemcpy3DParms p{};
     cudaPitchedPtr dn = make_cudaPitchedPtr(const_cast<void*>(dense), (size_t)L.nx * eb, (size_t)L.nx, (size_t)L.ny);

@@ -433,29 +433,25 @@ cudaError_t wave_run(const SweepArgs& a, void* const field[2], int p0, int T, co
                      long long* tile_passes) {
     if (T <= 0 || a.L.nx == 0 || a.L.ny == 0 || a.L.nz == 0) return cudaSuccess;
     if (!ws) return cudaErrorInvalidValue;
+#define STG_WR(KK, TTF, TTC) \
+    return wave_run_t<KK, TTF, TTC>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes)
     switch (a.kind) {
         case K7C:
-            if (a.fdt == DT_F32) return wave_run_t<K7C, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
-            if (a.fdt == DT_F64)
-                return wave_run_t<K7C, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
+            if (a.fdt == DT_F32) STG_WR(K7C, float, float);
+            if (a.fdt == DT_F64) STG_WR(K7C, double, double);
             break;
         case K7V:
-            if (a.fdt == DT_F32 && a.cdt == DT_F32)
-                return wave_run_t<K7V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
-            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return wave_run_t<K7V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
-            if (a.fdt == DT_F64)
-                return wave_run_t<K7V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WR(K7V, float, float);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WR(K7V, float, __nv_bfloat16);
+            if (a.fdt == DT_F64) STG_WR(K7V, double, double);
             break;
         case K25V:
-            if (a.fdt == DT_F32 && a.cdt == DT_F32)
-                return wave_run_t<K25V, float, float>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
-            if (a.fdt == DT_F32 && a.cdt == DT_BF16)
-                return wave_run_t<K25V, float, __nv_bfloat16>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
-            if (a.fdt == DT_F64)
-                return wave_run_t<K25V, double, double>(a, field, p0, T, tn, ws, ws_bytes, ctl, s, launches, tile_passes);
+            if (a.fdt == DT_F32 && a.cdt == DT_F32) STG_WR(K25V, float, float);
+            if (a.fdt == DT_F32 && a.cdt == DT_BF16) STG_WR(K25V, float, __nv_bfloat16);
+            if (a.fdt == DT_F64) STG_WR(K25V, double, double);
             break;
     }
+#undef STG_WR
     return cudaErrorInvalidValue;
 }
 

@@ -154,10 +154,11 @@ int stencil_set_field(stencil_t h, const void* src, double halo_value, int where
  * tiles of 32 vectors by `warps` rows (4, 8 or 16, >= R), the CTAs waiting on
  * bounded completion flags; xtile = 2 copies every load two planes ahead into
  * shared memory where nf >= R + 2 and it fits, 0 does not; xtile = 4 (25-point
- * stencil, FP32 field, 8 rows) stages whole tile planes (the field with its
- * halos, the 13 coefficient planes) in shared memory with tensor copies issued
- * by one producer warp, where every (level, tile) CTA fits on the GPU at once
- * (else the column walk runs); NULL: h = 2,
+ * stencil, FP32 field, 8 rows) stages the field's tile planes with their halos
+ * in shared memory by tensor copies issued by one producer warp, and each
+ * thread's coefficient vectors by its own asynchronous copies a plane or more
+ * ahead, where every (level, tile) CTA fits on the GPU at once (else the
+ * column walk runs); NULL: h = 2,
  * 8-plane chunks, 8 rows, no copies ahead; needs a bound workspace, else
  * STENCIL_EINVAL; bit-identical to the plain sweep), or
  * STENCIL_BLOCKED with *tuning (NULL: library default: D_w = 8R, N_F = 2 where it

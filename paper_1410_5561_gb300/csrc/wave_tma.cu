@@ -1,5 +1,5 @@
-// Wavefront pass of the 25-point stencil (Listing 3) with every operand staged in
-// shared memory by the tensor memory accelerator.
+// Wavefront pass of the 25-point stencil (Listing 3) with its operands staged in shared
+// memory: the field by the tensor memory accelerator, the coefficients by per-thread copies.
 //
 // The schedule is the stream form of the L2 wavefront (wavefront.cu): CTA (l, q)
 // computes time level l of the pass on xy tile q (128 columns by 8 rows) for all
@@ -9,16 +9,17 @@
 // own 24 vectors per plane (x, y and z neighbours, 13 coefficients) and waits a
 // full memory latency for them, and the 180 registers it needs leave room for 8
 // warps per SM. Here one producer warp copies, per plane, the tile's field plane
-// with its 4-cell x and y halos (one box) and the 13 coefficient planes of the
-// tile (13 boxes) into shared-memory rings, several planes ahead, and the 8
-// consumer warps read every operand from shared memory: the loads of a tile are
-// issued once per CTA instead of once per neighbour, and their latency is hidden
-// by the ring instead of by warps.
+// with its 4-cell x and y halos (one tensor box) into a shared-memory ring several
+// planes ahead, so the 11 neighbour vectors of a point group are read from shared
+// memory and each field value crosses L2 once per CTA. Each consumer thread copies
+// its own 13 coefficient vectors NCS - 1 planes ahead into slots of its own with
+// cp.async (no value is shared, so per-thread copies duplicate nothing; 13 tensor
+// boxes per plane proved slower: the copy engine takes about 100 ns per box).
 //
 //   field ring:        NFS slots of (136 x 16) FP32, plane p in slot (p + R) mod NFS
-//   coefficient ring:  NCS slots of 13 x (136 x 8) coefficients, plane z in slot z mod NCS
 //   mbarriers:         full (the copy's bytes landed) and empty (all 8 consumer warps
-//                      are done with the slot) per slot
+//                      are done with the slot) per field slot
+//   coefficient slots: NCS planes x 13 arrays x 256 threads x one vector
 //
 // Each update is evaluated by upd25v in Listing 3's order with the same operand
 // values as the plain sweep, so results are bit-identical to it.
@@ -42,18 +43,18 @@ template <typename TC>
 struct TwCfg {
     static constexpr int YH = TW_BY + 2 * TW_R;                   // field box rows
     static constexpr int FSB = TW_XW * YH * 4;                    // field slot bytes (8704)
-    static constexpr int CAB = TW_XW * TW_BY * (int)sizeof(TC);   // one coefficient array's plane
-    static constexpr int CSB = 13 * CAB;                          // coefficient slot bytes
+    static constexpr int CVB = 4 * (int)sizeof(TC);               // one thread's coefficient vector
+    static constexpr int CSB = 13 * 32 * TW_BY * CVB;             // one plane's per-thread slots
     static constexpr int NCS = sizeof(TC) == 4 ? 2 : 4;           // coefficient planes in flight + 1
     static constexpr int NFS = 2 * TW_R + 1 + NCS;                // the z window and the planes ahead
-    static constexpr int BAR = 2 * (NFS + NCS) * 8;
+    static constexpr int BAR = 2 * NFS * 8;
     static constexpr size_t SMEM = (size_t)NFS * FSB + (size_t)NCS * CSB + BAR;
-    static_assert(FSB % 128 == 0 && CAB % 128 == 0, "box destinations stay 128-byte aligned");
+    static_assert(FSB % 128 == 0, "box destinations stay 128-byte aligned");
 };
 
 struct TwArgs {
     CUtensorMap fmap[2];     // the two field arrays, box (136, 16, 1)
-    CUtensorMap cmap[13];    // coefficient arrays, box (136, 8, 1)
+    const void* cf[13];      // coefficient arrays
     Layout L;
     float* lv[TW_MAXLV + 1];  // level l writes lv[l + 1]
     int lvmap[TW_MAXLV];      // level l reads the array of fmap[lvmap[l]]
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
     const uint32_t fring = tma_smem(tw_smem);
     const uint32_t cring = fring + NFS * Cfg::FSB;
     const uint32_t bars = cring + NCS * Cfg::CSB;
-    const uint32_t ffull = bars, fempty = bars + 8 * NFS, cfull = bars + 16 * NFS, cempty = bars + 16 * NFS + 8 * NCS;
+    const uint32_t ffull = bars, fempty = bars + 8 * NFS;
     const int ntiles = A.ntx * A.nty;
     const int l = (int)blockIdx.x / ntiles, q = (int)blockIdx.x % ntiles;
     const int qx = q % A.ntx, qy = q / A.ntx;
@@ -130,10 +131,6 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
         for (int s = 0; s < NFS; ++s) {
             mbar_init(ffull + 8 * s, 1);
             mbar_init(fempty + 8 * s, BY);
-        }
-        for (int s = 0; s < NCS; ++s) {
-            mbar_init(cfull + 8 * s, 1);
-            mbar_init(cempty + 8 * s, BY);
         }
         mbar_init_fence();
     }
@@ -180,33 +177,14 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
             }
             __syncwarp();
         };
-        auto issue_coef = [&](int z) {  // the 13 coefficient planes z of the tile
-            if (lane == 0) {
-                const int s = z % NCS, u = z / NCS;
-                if (u > 0) mbar_wait(cempty + 8 * s, (uint32_t)((u - 1) & 1), A.status);
-                mbar_arrive_expect_tx(cfull + 8 * s, (uint32_t)Cfg::CSB);
-                const uint32_t d = cring + (uint32_t)(s * Cfg::CSB);
-#pragma unroll 1
-                for (int m = 0; m < 13; ++m)
-                    tma_load_3d(d + (uint32_t)(m * Cfg::CAB), &A.cmap[m], xs, y0 + R, z + R, cfull + 8 * s);
-            }
-            __syncwarp();
-        };
         for (int p = -R; p < R; ++p) issue_field(p);
-        for (int z = 0; z < nz; ++z) {
-            issue_field(z + R);
-            issue_coef(z);
-        }
+        for (int z = 0; z < nz; ++z) issue_field(z + R);
         // no copy may be in flight when the CTA exits: wait (bounded) for each slot's last phase
         if (lane == 0) {
             const int nf = nz + 2 * R;
             for (int s = 0; s < NFS && s < nf; ++s) {
                 const int u = (nf - 1 - s) / NFS;  // last use of slot s
                 mbar_wait(ffull + 8 * s, (uint32_t)(u & 1), A.status);
-            }
-            for (int s = 0; s < NCS && s < nz; ++s) {
-                const int u = (nz - 1 - s) / NCS;
-                mbar_wait(cfull + 8 * s, (uint32_t)(u & 1), A.status);
             }
         }
         return;
@@ -219,7 +197,24 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
     float* const dst = A.lv[l + 1];
     constexpr uint32_t RB = TW_XW * 4;  // field box row bytes
     const uint32_t frow = (uint32_t)(((warp + R) * TW_XW + R + lane * 4) * 4);   // the vector in a field slot
-    const uint32_t crow = (uint32_t)((warp * TW_XW + R + lane * 4) * (int)sizeof(TC));
+    const uint32_t cslot = cring + (uint32_t)(threadIdx.x * Cfg::CVB);  // + (plane slot * 13 + m) * 256 CVB
+    auto coef_copy = [&](int p) {  // this thread's 13 coefficient vectors of plane p into its slots
+        if (act && p < nz) {
+            const size_t g = A.L.at(i0, j, p);
+            const uint32_t d = cslot + (uint32_t)((p % NCS) * Cfg::CSB);
+#pragma unroll
+            for (int m = 0; m < 13; ++m) {
+                const char* src = static_cast<const char*>(A.cf[m]) + g * sizeof(TC);
+                const uint32_t dst = d + (uint32_t)(m * 32 * BY * Cfg::CVB);
+                if constexpr (sizeof(TC) == 4)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+                else
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int p = 0; p < NCS - 1; ++p) coef_copy(p);
     for (int it = 0; it < 2 * R; ++it) mbar_wait(ffull + 8 * (it % NFS), (uint32_t)((it / NFS) & 1), A.status);
     size_t gidx = A.L.at(i0, j, 0);
     const size_t sz = A.L.plane();
@@ -227,7 +222,9 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
         {
             const int it = z + 2 * R;  // field plane z + R
             mbar_wait(ffull + 8 * (it % NFS), (uint32_t)((it / NFS) & 1), A.status);
-            mbar_wait(cfull + 8 * (z % NCS), (uint32_t)((z / NCS) & 1), A.status);
+            coef_copy(z + NCS - 1);  // into the slot of plane z - 1, whose values are consumed
+            if constexpr (NCS == 2) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            else asm volatile("cp.async.wait_group 3;\n" ::: "memory");
         }
         auto fslot = [&](int p) { return fring + (uint32_t)(((p + R) % NFS) * Cfg::FSB) + frow; };
         const uint32_t fc = fslot(z);
@@ -250,9 +247,9 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
             zm[d - 1] = tw_ld4(fslot(z - d));
         }
         float cv[13][4];
-        const uint32_t cb = cring + (uint32_t)((z % NCS) * Cfg::CSB) + crow;
+        const uint32_t cb = cslot + (uint32_t)((z % NCS) * Cfg::CSB);
 #pragma unroll
-        for (int m = 0; m < 13; ++m) CoefVec<TC>::ld(cb + (uint32_t)(m * Cfg::CAB), cv[m]);
+        for (int m = 0; m < 13; ++m) CoefVec<TC>::ld(cb + (uint32_t)(m * 32 * BY * Cfg::CVB), cv[m]);
         Vec<float, 4> out;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -283,7 +280,6 @@ __global__ void __launch_bounds__(32 * (TW_BY + 1), 1) wave_tma_kernel(const __g
         __syncwarp();
         if (lane == 0) {
             mbar_arrive(fempty + 8 * (z % NFS));  // plane z - R: slot (z - R + R) mod NFS
-            mbar_arrive(cempty + 8 * (z % NCS));
         }
         if (z % A.zc == A.zc - 1 || z == nz - 1) {  // chunk z / zc finished by every consumer warp
             asm volatile("bar.sync 1, %0;\n" ::"r"(32 * BY) : "memory");
@@ -344,14 +340,12 @@ cudaError_t wave_tma_t(const SweepArgs& a, void* const* lvl, int h, const WaveTu
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kfn, 32 * (TW_BY + 1), Cfg::SMEM))) return e;
     if (ctas > (long long)per * sms) return cudaErrorNotReady;  // every (level, tile) CTA must be resident
     TwArgs A{};
-    const CUtensorMapDataType cdt = sizeof(TC) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     if (!encode_3d(&A.fmap[0], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, lvl[0], L, TW_XW, TW_BY + 2 * TW_R))
         return cudaErrorNotReady;
     if (!encode_3d(&A.fmap[1], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h > 1 ? lvl[1] : lvl[0], L, TW_XW,
                    TW_BY + 2 * TW_R))
         return cudaErrorNotReady;
-    for (int m = 0; m < 13; ++m)
-        if (!encode_3d(&A.cmap[m], cdt, (int)sizeof(TC), a.coef[m], L, TW_XW, TW_BY)) return cudaErrorNotReady;
+    for (int m = 0; m < 13; ++m) A.cf[m] = a.coef[m];
     A.L = L;
     for (int lv = 0; lv <= h; ++lv) A.lv[lv] = static_cast<float*>(lvl[lv]);
     for (int lv = 0; lv < h; ++lv) A.lvmap[lv] = lv & 1;
